@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the matrix-valued quantum LBM step on GB300.
+
+Default workload: D3Q19 128^3 periodic, tau = 0.7, beta0 = 1, density,
+velocity (|u| <= 0.05) and spin fields as seeded Fourier-mode sums with
+|k| <= 4, equilibrium-initialised (the 3D FP64/FP32 configuration).  One
+"step" is one time step of the whole forward path: the fused
+moments + equilibrium + BGK + in-place streaming kernel; the timed region
+ends with the FP64 conservation reduction.  Reported:
+
+  value       MLUPS of the FP32-storage step (sites x steps / s / 1e6)
+  roofline    the step kernel's algorithmic bytes (b*4 values read + written
+              per site) / its CUDA-event duration, against the measured HBM
+              copy bandwidth
+  fp64        the same for FP64 storage
+  e2e         MLUPS through the C ABI with host buffers: init from pinned
+              host fields, K steps, moments back to pinned host memory
+  cpu_baseline  the FP64 oracle on a 32^3 sample on the host cores
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (the path has
+no exchange step in this build); value = all ranks' site updates / max time.
+"""
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline (FP64 vs FP32 storage), adjoint/forward time ratio"
+
+WORKLOADS = {
+    "d3q19-128": dict(d=3, dims=(128, 128, 128), tau=0.7, beta0=1.0, kind="modes", seed=2,
+                      desc="D3Q19 128^3 periodic, tau=0.7, beta0=1, Fourier-mode density/velocity/spin "
+                           "fields |k|<=4 (RMS 0.02, |u|<=0.05), equilibrium init, eps=eps0"),
+    "d3q19-512": dict(d=3, dims=(512, 512, 512), tau=0.6, beta0=1.0, kind="modes", seed=5,
+                      desc="D3Q19 512^3 periodic, tau=0.6, beta0=1, Fourier-mode fields amplitude 0.02"),
+    "d2q9-4096": dict(d=2, dims=(4096, 4096, 1), tau=0.7, beta0=1.0, kind="shear", seed=3,
+                      desc="D2Q9 4096^2 periodic double shear layer, opposite spin bands"),
+}
+
+
+def bytes_per_value(prec):
+    return {"fp64": 8, "fp32": 4, "fp16dev": 2}[prec]
+
+
+def make_fields(w):
+    from paper_1309_1656_gb300 import fields
+    if w["kind"] == "modes":
+        return fields.modes(w["d"], w["dims"], seed=w["seed"])
+    if w["kind"] == "shear":
+        return fields.shear2d(w["dims"][0], w["dims"][1], seed=w["seed"])
+    raise ValueError(w["kind"])
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1309_1656_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per site of a kernel from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_site"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", dev_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) != 7:
+                    continue
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_device(lat, K, W, stream, torch):
+    """W warm-up steps, then K timed steps + the conservation reduction.
+    Returns (step_ms_avg, total_ms)."""
+    lat.step(W)
+    lat.sync()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(K)
+    e1.record(stream)
+    cons = lat.conserved()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / K, e0.elapsed_time(e2), cons
+
+
+def bench_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    from paper_1309_1656_gb300 import _build
+    if not _build.up_to_date():
+        if rank == 0:
+            __graft_entry__.build()
+        if ws > 1:
+            torch.distributed.barrier()
+    from paper_1309_1656_gb300 import qlbm
+
+    w = WORKLOADS[args.workload]
+    d, dims = w["d"], w["dims"]
+    N = dims[0] * dims[1] * dims[2]
+    b = 9 if d == 2 else 19
+    K, W = args.steps, args.warmup
+    fl = make_fields(w)
+    peak, peak_src = measured_peaks()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "")) or str(dev)
+    dev_id = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if len(uuid) > 30 else str(dev))
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    clocks = None
+    for prec in args.precisions.split(","):
+        lat = qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision=prec, stream=stream.cuda_stream)
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        c0 = lat.conserved()
+        barrier()
+        sampler = ClockSampler(dev_id) if prec == "fp32" else None
+        step_ms, total_ms, c1 = run_device(lat, K, W, stream, torch)
+        if sampler is not None:
+            clocks = sampler.stop()
+        step_ms = max_over_ranks(step_ms)
+        total_ms = max_over_ranks(total_ms)
+        alg_bytes = N * b * 4 * 2 * bytes_per_value(prec)
+        achieved = alg_bytes / (step_ms * 1e-3) / 1e9
+        drift = float(np.max(np.abs(c1 - c0)) / np.max(np.abs(c0)))
+        results[prec] = dict(step_ms=step_ms, total_ms=total_ms, achieved=achieved,
+                             mlups=ws * N * K / (total_ms * 1e-3) / 1e6,
+                             kernel_mlups=ws * N / (step_ms * 1e-3) / 1e6, drift=drift,
+                             alg_bytes=alg_bytes)
+        lat.close()
+        del lat
+        torch.cuda.synchronize()
+
+    # end-to-end through the C ABI with pinned host buffers
+    e2e = None
+    if "fp32" in results and not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        r4, uu = pin(fl["rho4"]), pin(fl["u"])
+        out_r = torch.empty((4, N), dtype=torch.float64).pin_memory().numpy()
+        out_u = torch.empty((d, N), dtype=torch.float64).pin_memory().numpy()
+        out_e = torch.empty((N,), dtype=torch.float64).pin_memory().numpy()
+        lat = qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision="fp32", stream=stream.cuda_stream)
+        lat.init_equilibrium(r4, uu)       # warm the staging buffers
+        lat.step(W)
+        qlbm.qlbm_moments(lat.h, out_r, out_u, out_e)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qlbm.qlbm_init_equilibrium(lat.h, r4, uu, None)
+        qlbm.qlbm_step(lat.h, K)
+        qlbm.qlbm_moments(lat.h, out_r, out_u, out_e)
+        t1 = time.perf_counter()
+        dt_e2e = max_over_ranks(t1 - t0)
+        lat.close()
+        e2e = {"value": round(ws * N * K / dt_e2e / 1e6, 3), "unit": "MLUPS",
+               "h2d_bytes_per_step": (r4.nbytes + uu.nbytes) / K,
+               "d2h_bytes_per_step": (out_r.nbytes + out_u.nbytes + out_e.nbytes) / K}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, target_s=args.cpu_seconds)
+
+    r32 = results.get("fp32") or next(iter(results.values()))
+    prim = "fp32" if "fp32" in results else next(iter(results))
+    traffic = recorded_traffic("step_%s_d%d" % (prim, d))
+    roof = {"bound": "hbm", "achieved": round(r32["achieved"], 1), "peak": peak, "unit": "GB/s",
+            "frac": round(r32["achieved"] / peak, 4), "peak_source": peak_src,
+            "traffic": None if traffic is None else round(traffic * N),
+            "algorithmic_bytes_per_launch": r32["alg_bytes"],
+            "kernel": "k_step_aa<%d,%s>" % (d, prim)}
+    line = {
+        "metric": METRIC, "value": round(r32["mlups"], 1), "unit": "MLUPS", "n_gpus": ws,
+        "steps": K, "warmup": W, "ms_per_step": round(r32["total_ms"] / K, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32"}[prim],
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "lattice": "D3Q19" if d == 3 else "D2Q9",
+                   "dims": list(dims), "sites": N, "tau": w["tau"], "beta0": w["beta0"],
+                   "precision": prim, "parallelism": "replicas" if ws > 1 else "single-gpu",
+                   "l2": "inputs larger than L2: state %.2f GB > 129 MB, no flush" %
+                         (N * b * 4 * bytes_per_value(prim) / 1e9)},
+        "roofline": roof,
+        "kernel_mlups": round(r32["kernel_mlups"], 1),
+        "conservation_drift_rel": r32["drift"],
+        "gpu_launches": K + 2,
+    }
+    if "fp64" in results:
+        r = results["fp64"]
+        line["fp64"] = {"value": round(r["mlups"], 1), "unit": "MLUPS",
+                        "kernel_mlups": round(r["kernel_mlups"], 1),
+                        "achieved_gbs": round(r["achieved"], 1), "hbm_frac": round(r["achieved"] / peak, 4),
+                        "conservation_drift_rel": r["drift"]}
+    if clocks:
+        line["clocks"] = clocks
+    if e2e:
+        line["e2e"] = e2e
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_sample(w, L=32):
+    from paper_1309_1656_gb300 import fields
+    d = w["d"]
+    dims = (L, L, L) if d == 3 else (L * 8, L * 8, 1)
+    fl = fields.modes(d, dims, seed=w["seed"]) if w["kind"] == "modes" else \
+        fields.shear2d(dims[0], dims[1], seed=w["seed"], delta=max(2.0, 80.0 * dims[1] / 4096.0))
+    return dims, fl
+
+
+def cpu_baseline(w, target_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    d = w["d"]
+    dims, fl = cpu_sample(w)
+    N = dims[0] * dims[1] * dims[2]
+    cores = oracle.max_threads(0)
+    st = oracle.init_equilibrium(d, dims, w["beta0"], fl["rho4"], fl["u"], fl["eps"])
+    t = time.perf_counter()
+    st = oracle.run(d, dims, w["tau"], w["beta0"], 1, st)
+    t1 = time.perf_counter() - t
+    n = int(max(1, min(2000, target_s / max(t1, 1e-6))))
+    t = time.perf_counter()
+    oracle.run(d, dims, w["tau"], w["beta0"], n, st)
+    dt = time.perf_counter() - t
+    return {"value": round(N * n / dt / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%s sub-lattice %s of the same workload recipe, %d FP64 steps, %.1f s" %
+                      ("D3Q19" if d == 3 else "D2Q9", "x".join(map(str, dims)), n, dt)}
+
+
+def bench_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = WORKLOADS[args.workload]
+    d = w["d"]
+    dims, fl = cpu_sample(w)
+    N = dims[0] * dims[1] * dims[2]
+    cores = oracle.max_threads(0)
+    st = oracle.init_equilibrium(d, dims, w["beta0"], fl["rho4"], fl["u"], fl["eps"])
+    st = oracle.run(d, dims, w["tau"], w["beta0"], args.warmup, st)
+    t = time.perf_counter()
+    oracle.run(d, dims, w["tau"], w["beta0"], args.steps, st)
+    dt = time.perf_counter() - t
+    v = N * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["desc"], "sample": "x".join(map(str, dims)),
+                       "note": "reference arm = the FP64 CPU oracle (no reference implementation exists)"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": "%s sub-lattice %s per step" %
+                                       ("D3Q19" if d == 3 else "D2Q9", "x".join(map(str, dims)))},
+            "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="d3q19-128", choices=sorted(WORKLOADS))
+    ap.add_argument("--precisions", default="fp32,fp64")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * qlbm.h -- C ABI of a GB300 (sm_103a) library for the matrix-valued quantum
+ * lattice Boltzmann method of C. B. Mendl, "Matrix-valued Quantum Lattice
+ * Boltzmann Method" (2015).
+ *
+ * The library advances populations W_i(x,t), each a Hermitian 2x2 matrix
+ * (Sec. 2), on a periodic D2Q9 or D3Q19 lattice (Sec. 3) with the step of
+ * Sec. 3.3: moments (Eq. DiscrAvr), polynomial Fermi-Dirac equilibrium
+ * (Eq. WeqAlgo, coefficients of the appendix), BGK collision
+ * (Eq. CollisionStep) and streaming (Eq. TransportStep).  All compute runs in
+ * the library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: QLBM_D2Q9 (d = 2, b = 9) or QLBM_D3Q19 (d = 3, b = 19).  Direction
+ *   q has lattice vector i_q in {-1,0,1}^d (D3Q19: |i1|+|i2|+|i3| <= 2) and
+ *   velocity e_q = xi * i_q (Sec. 3.1); q enumerates the vectors with i1
+ *   varying fastest, then i2, then i3, so the opposite of q is b-1-q.
+ * Sites: dims = {nx, ny, nz} (nz = 1 for D2Q9), N = nx*ny*nz, flat site
+ *   index s = x + nx*(y + ny*z), periodic in every direction (Sec. 3).
+ * Pauli form: a Hermitian W is given by four reals (f, s_x, s_y, s_z) with
+ *   W = (f 1 + s_x sigma_x + s_y sigma_y + s_z sigma_z)/2, i.e. f = tr W and
+ *   s = tr(W sigma), the Bloch-vector convention of Sec. 4.
+ * Canonical state layout: double [b][4][N] (direction, Pauli component,
+ *   site); this is the order of get/set_state and of adjoint cotangents.
+ * Moment fields: rho4 double [4][N] = (tr rho, tr(rho sigma_x),
+ *   tr(rho sigma_y), tr(rho sigma_z)); u double [d][N]; eps double [N].
+ * Units: tau and dt in the same time unit, omega = dt/tau (Eq. CollisionStep);
+ *   streaming moves one cell per step (dt xi = dx, Sec. 3.3).
+ * Pointers: every pointer argument is owned by the caller and only read or
+ *   written during the call (asynchronously on the handle's stream for
+ *   device pointers, see each entry point); ptr_kind says whether it is host
+ *   memory (QLBM_HOST) or device memory of the handle's GPU (QLBM_DEVICE).
+ *   Host buffers are copied synchronously.  The library owns all memory it
+ *   allocates and frees it in qlbm_destroy.
+ * Errors: every int-returning call returns QLBM_OK (0) or a negative
+ *   qlbm_status; no exception crosses the ABI.  The message of the last
+ *   failure is available from qlbm_last_error.  The step kernels record
+ *   non-finite or non-positive densities in a device flag word that the next
+ *   synchronising call (qlbm_sync, qlbm_moments, qlbm_conserved,
+ *   qlbm_get_state, qlbm_rollout_adjoint) reports and clears.
+ * Streams: all device work is issued on the stream given to qlbm_create
+ *   (NULL = the legacy default stream).  A handle must not be used from two
+ *   host threads at once.
+ */
+#ifndef QLBM_H
+#define QLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum qlbm_status {
+    QLBM_OK = 0,
+    QLBM_ERR_INVALID_ARG = -1,        /* bad size, pointer, parameter or lattice */
+    QLBM_ERR_UNSUPPORTED = -2,        /* combination not provided by this build */
+    QLBM_ERR_OOM = -3,                /* device allocation failed */
+    QLBM_ERR_CUDA = -4,               /* a CUDA runtime call failed */
+    QLBM_ERR_NONFINITE = -5,          /* a step met a NaN or infinite moment */
+    QLBM_ERR_NONPOSITIVE_DENSITY = -6,/* a step met tr rho <= 0 */
+    QLBM_ERR_STATE = -7               /* call not valid in the handle's state */
+} qlbm_status;
+
+typedef enum qlbm_lattice { QLBM_D2Q9 = 2, QLBM_D3Q19 = 3 } qlbm_lattice;
+
+/* Storage precision of the populations.  QLBM_FP64 computes in double;
+   QLBM_FP32 stores and computes in float; QLBM_FP16_DEV stores the deviation
+   W_i - W_i^ref from a uniform reference equilibrium in half precision and
+   computes in float. */
+typedef enum qlbm_precision { QLBM_FP64 = 0, QLBM_FP32 = 1, QLBM_FP16_DEV = 2 } qlbm_precision;
+
+typedef enum qlbm_ptr_kind { QLBM_HOST = 0, QLBM_DEVICE = 1 } qlbm_ptr_kind;
+
+typedef struct qlbm_ctx *qlbm_handle;
+
+/* qlbm_create -- set up a lattice (Sec. 3.3: "The framework takes as input the
+ * relaxation time tau and a reference inverse temperature beta0").
+ *   out        receives the handle (unchanged on failure)
+ *   lattice    QLBM_D2Q9 or QLBM_D3Q19
+ *   dims       {nx, ny, nz}; nz must be 1 for D2Q9; every entry >= 1
+ *   tau        relaxation time, > 0
+ *   beta0      reference inverse temperature of the quadrature (Sec. 3.1), > 0;
+ *              fixes xi = const/sqrt(beta0) and the weights (Eqs.
+ *              QuadSolution2Dmu0, QuadSolution3Dmu0)
+ *   dt         time step, > 0 (omega = dt/tau)
+ *   precision  qlbm_precision
+ *   stream     cudaStream_t to issue work on, or NULL
+ * Allocates the single in-place population buffer (b*4*N values of the
+ * storage type, padded per plane) and small scratch on the current device.
+ * The state is undefined until qlbm_init_equilibrium or qlbm_set_state.
+ * Returns QLBM_ERR_OOM if the buffer does not fit. */
+int qlbm_create(qlbm_handle *out, int lattice, const int64_t dims[3], double tau,
+                double beta0, double dt, int precision, void *stream);
+
+/* Releases all device memory of the handle (after synchronising its stream).
+   NULL is accepted. */
+void qlbm_destroy(qlbm_handle h);
+
+/* Message of the most recent failure on this handle, or of the last failed
+   qlbm_create when h is NULL.  Valid until the next call on the handle. */
+const char *qlbm_last_error(qlbm_handle h);
+
+/* qlbm_info -- the lattice constants this handle uses, computed in double on
+ * the host at qlbm_create from the quadrature's moment conditions (Eqs.
+ * quadrature2D/3D) and the equilibrium's (Sec. 3.2, appendix).
+ * out[0..15] = {d, b, xi, a, w_rest, w_axis, w_diag, beta0*eps0 (= c),
+ *               beta0^2 <(p^2/2)^2>_0 (= m), alpha3, alpha4, alpha5,
+ *               tau, beta0, dt, precision}; n must be >= 16. */
+int qlbm_info(qlbm_handle h, double *out, int n);
+
+/* qlbm_init_equilibrium -- initial state W_i(x,t0) = W_i^eq(rho(x), u(x),
+ * eps(x)) of Eq. WeqAlgo at every site (the paper's input "an initial
+ * configuration of distribution functions", Sec. 3.3).
+ *   rho4  [4][N] Pauli density (tr rho must be > 0)
+ *   u     [d][N] velocity
+ *   eps   [N] internal energy, or NULL for eps0, the internal energy of the
+ *         quadrature's own Fermi-Dirac weight (beta0, mu0 = 0)
+ * Resets the step counter to 0.  Device inputs are read on the stream;
+ * host inputs are staged through the library and copied before return. */
+int qlbm_init_equilibrium(qlbm_handle h, const double *rho4, const double *u,
+                          const double *eps, int ptr_kind);
+
+/* qlbm_step -- nsteps >= 0 time steps t -> t + dt of Sec. 3.3, each one
+ * fused kernel launch (moments, equilibrium, collision and in-place
+ * streaming).  Asynchronous: returns after queueing the launches. */
+int qlbm_step(qlbm_handle h, int64_t nsteps);
+
+/* Number of steps taken since the last init/set_state. */
+int64_t qlbm_time(qlbm_handle h);
+
+/* Waits for the handle's stream and reports (then clears) the step kernels'
+   device flags as QLBM_ERR_NONFINITE / QLBM_ERR_NONPOSITIVE_DENSITY. */
+int qlbm_sync(qlbm_handle h);
+
+/* qlbm_moments -- local moments of Eq. DiscrAvr at the current time:
+ * rho4 [4][N], u [d][N], eps [N] (any of the three may be NULL).  Computed
+ * in double from the stored populations.  Synchronising. */
+int qlbm_moments(qlbm_handle h, double *rho4, double *u, double *eps, int ptr_kind);
+
+/* qlbm_conserved -- global averages of Eqs. GlobalDensity, GlobalVelocity
+ * and GlobalTotalEnergy, reduced in double on the device (deterministic):
+ *   out[0..3] = Pauli components of (1/|Lambda|) sum_x rho(x)
+ *   out[4..6] = (1/|Lambda|) sum_x sum_i e_i tr W_i   (zero beyond d)
+ *   out[7]    = (1/|Lambda|) sum_x sum_i |e_i|^2/2 tr W_i
+ * out is host memory of 8 doubles.  Synchronising. */
+int qlbm_conserved(qlbm_handle h, double *out);
+
+/* qlbm_get_state / qlbm_set_state -- the populations at the current time in
+ * the canonical layout double [b][4][N] (checkpoint and exchange format).
+ * set_state resets the step counter to 0; values are rounded to the storage
+ * precision.  get_state is synchronising. */
+int qlbm_get_state(qlbm_handle h, double *buf, int ptr_kind);
+int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QLBM_H */

@@ -37,10 +37,23 @@ _pd = ctypes.POINTER(ctypes.c_double)
 _pi64 = ctypes.POINTER(ctypes.c_int64)
 
 
+def _same_arch(path):
+    """True if the ELF file was built for this machine's architecture."""
+    import platform
+    want = {"x86_64": 62, "amd64": 62, "aarch64": 183, "arm64": 183}.get(platform.machine().lower())
+    try:
+        with open(path, "rb") as f:
+            h = f.read(20)
+    except OSError:
+        return False
+    return h[:4] == b"\x7fELF" and int.from_bytes(h[18:20], "little") == want
+
+
 def build(force=False):
     """Compile the oracle with gcc (no FMA contraction, OpenMP over sites)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    if (not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
+            and _same_arch(_LIB)):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fopenmp",

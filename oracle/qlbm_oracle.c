@@ -330,7 +330,7 @@ static void state_to_pauli(const lattice *L, const grid *G, const mat2 *W, doubl
 static int set_threads(int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());
     return omp_get_max_threads();
 #else
     (void)nthreads;

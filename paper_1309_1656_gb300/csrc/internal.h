@@ -1,0 +1,83 @@
+// Host-side context of a lattice and the per-lattice kernel dispatch table.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/qlbm.h"
+#include "lattice.cuh"
+
+namespace qlbm {
+
+// Lattice constants in double, derived on the host from the quadrature's and
+// the equilibrium's moment conditions (see consts.cu).
+struct HostConsts {
+    int d, b;
+    double beta0;
+    double c, m;          // beta0 <w>_0 and beta0^2 <w^2>_0, w = |p|^2/2
+    double xi, a;
+    double w[3];          // weights by |i|^2 = 0, 1, 2
+    double alpha3, alpha4, alpha5;
+    double K;             // beta0 xi^2 / 2
+    double eps0;          // c / beta0
+};
+
+int compute_constants(int d, double beta0, HostConsts *out);
+
+struct LatticeOps;
+
+}  // namespace qlbm
+
+struct qlbm_ctx {
+    int d = 0, b = 0, prec = 0;
+    qlbm::Grid g{};
+    double tau = 0, beta0 = 0, dt = 0;
+    qlbm::HostConsts hc{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    void *pop = nullptr;            // b*4*P elements of the storage type
+    size_t elem_bytes = 0;
+    int parity = 0;                 // 1: last written by an even step (swapped)
+    int64_t t = 0;                  // steps since init/set_state
+    unsigned *flags = nullptr;      // device flag word
+    double *partials = nullptr;     // device reduction scratch [nred][8]
+    double *red_out = nullptr;      // device [8]
+    int nred = 0;
+    double *staging = nullptr;      // device staging for host inputs/outputs
+    size_t staging_bytes = 0;
+    float fref[3] = {0, 0, 0};      // FP16 deviation reference by |i|^2
+    const qlbm::LatticeOps *ops = nullptr;
+    std::string err;
+};
+
+namespace qlbm {
+
+struct LatticeOps {
+    cudaError_t (*step)(qlbm_ctx *h, bool odd);
+    cudaError_t (*init_eq)(qlbm_ctx *h, const double *rho4, const double *u, const double *eps);
+    cudaError_t (*get_state)(qlbm_ctx *h, double *out);
+    cudaError_t (*set_state)(qlbm_ctx *h, const double *in);
+    cudaError_t (*moments)(qlbm_ctx *h, double *rho4, double *u, double *eps);
+    cudaError_t (*conserved_partial)(qlbm_ctx *h);
+};
+
+const LatticeOps *lattice_ops_d2q9(int prec);
+const LatticeOps *lattice_ops_d3q19(int prec);
+
+cudaError_t launch_conserved_final(qlbm_ctx *h);
+
+// Launch shape of the per-site kernels: one thread per site, blocks of up to
+// kStepBlock consecutive x in one row.
+inline dim3 site_block(const Grid &g)
+{
+    int bx = g.nx >= 128 ? 128 : ((g.nx + 31) / 32) * 32;
+    return dim3(bx);
+}
+inline dim3 site_grid(const Grid &g, int bx)
+{
+    return dim3((unsigned)((int64_t)g.nxb * g.ny * g.nz));
+}
+
+}  // namespace qlbm

@@ -1,0 +1,150 @@
+// Host launchers of the forward kernels for one lattice, gathered into a
+// dispatch table per storage precision.  Included by exactly one translation
+// unit per lattice.
+#pragma once
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace qlbm {
+
+template <typename R> Coll<R> make_coll(const qlbm_ctx *h)
+{
+    const HostConsts &k = h->hc;
+    const double omega = h->dt / h->tau;
+    Coll<R> c;
+    c.K = (R)k.K;
+    c.c = (R)k.c;
+    c.inv_mc2 = (R)(1.0 / (k.m - k.c * k.c));
+    c.c3 = (R)(2.0 * k.K * k.alpha3);
+    c.c4 = (R)(4.0 * k.K * k.K * k.alpha4);
+    c.c5 = (R)(k.K * k.alpha5);
+    c.omega = (R)omega;
+    c.omc = (R)(1.0 - omega);
+    for (int i = 0; i < 3; ++i) c.ow[i] = (R)(omega * k.w[i]);
+    return c;
+}
+
+inline InitConsts make_init(const qlbm_ctx *h)
+{
+    const HostConsts &k = h->hc;
+    InitConsts ic;
+    ic.xi = k.xi;
+    ic.K = k.K;
+    ic.c = k.c;
+    ic.inv_mc2 = 1.0 / (k.m - k.c * k.c);
+    ic.c3 = 2.0 * k.K * k.alpha3;
+    ic.c4 = 4.0 * k.K * k.K * k.alpha4;
+    ic.c5 = k.K * k.alpha5;
+    ic.eps0 = k.eps0;
+    ic.beta0 = k.beta0;
+    for (int i = 0; i < 3; ++i) ic.w[i] = k.w[i];
+    return ic;
+}
+
+template <class Codec> Codec make_codec(const qlbm_ctx *h);
+template <> inline CodecF64 make_codec<CodecF64>(const qlbm_ctx *) { return CodecF64{}; }
+template <> inline CodecF32 make_codec<CodecF32>(const qlbm_ctx *) { return CodecF32{}; }
+template <> inline CodecF16Dev make_codec<CodecF16Dev>(const qlbm_ctx *h)
+{
+    CodecF16Dev c;
+    for (int i = 0; i < 3; ++i) c.fref[i] = h->fref[i];
+    return c;
+}
+
+template <int D, class Codec> struct Launchers {
+    using S = typename Codec::S;
+    using R = typename Codec::R;
+    static constexpr int Q = Lattice<D>::Q;
+
+    static Planes<S, Q> planes(const qlbm_ctx *h)
+    {
+        Planes<S, Q> pl;
+        S *base = static_cast<S *>(h->pop);
+        for (int k = 0; k < 4 * Q; ++k) pl.p[k] = base + (int64_t)k * h->g.P;
+        return pl;
+    }
+
+    static cudaError_t step(qlbm_ctx *h, bool odd)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        const Planes<S, Q> pl = planes(h);
+        const Coll<R> k = make_coll<R>(h);
+        const Codec codec = make_codec<Codec>(h);
+        if (odd)
+            k_step_aa<D, Codec, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+        else
+            k_step_aa<D, Codec, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t init_eq(qlbm_ctx *h, const double *rho4, const double *u, const double *eps)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        k_init_eq<D, Codec><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_init(h),
+                                                        make_codec<Codec>(h), rho4, u, eps);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t get_state(qlbm_ctx *h, double *out)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        const Planes<S, Q> pl = planes(h);
+        if (h->parity)
+            k_get_state<D, Codec, true><<<grd, blk, 0, h->stream>>>(pl, h->g, make_codec<Codec>(h), out);
+        else
+            k_get_state<D, Codec, false><<<grd, blk, 0, h->stream>>>(pl, h->g, make_codec<Codec>(h), out);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t set_state(qlbm_ctx *h, const double *in)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        k_set_state<D, Codec><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_codec<Codec>(h), in);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t moments(qlbm_ctx *h, double *rho4, double *u, double *eps)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        const Planes<S, Q> pl = planes(h);
+        if (h->parity)
+            k_moments<D, Codec, true><<<grd, blk, 0, h->stream>>>(pl, h->g, make_codec<Codec>(h),
+                                                                  h->hc.xi, rho4, u, eps);
+        else
+            k_moments<D, Codec, false><<<grd, blk, 0, h->stream>>>(pl, h->g, make_codec<Codec>(h),
+                                                                   h->hc.xi, rho4, u, eps);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t conserved_partial(qlbm_ctx *h)
+    {
+        const Planes<S, Q> pl = planes(h);
+        if (h->parity)
+            k_conserved_partial<D, Codec, true><<<h->nred, kRedBlock, 0, h->stream>>>(
+                pl, h->g, make_codec<Codec>(h), h->partials);
+        else
+            k_conserved_partial<D, Codec, false><<<h->nred, kRedBlock, 0, h->stream>>>(
+                pl, h->g, make_codec<Codec>(h), h->partials);
+        return cudaGetLastError();
+    }
+
+    static const LatticeOps *table()
+    {
+        static const LatticeOps t = {&step, &init_eq, &get_state, &set_state, &moments,
+                                     &conserved_partial};
+        return &t;
+    }
+};
+
+template <int D> const LatticeOps *ops_for(int prec)
+{
+    switch (prec) {
+    case QLBM_FP64: return Launchers<D, CodecF64>::table();
+    case QLBM_FP32: return Launchers<D, CodecF32>::table();
+    case QLBM_FP16_DEV: return Launchers<D, CodecF16Dev>::table();
+    default: return nullptr;
+    }
+}
+
+}  // namespace qlbm

@@ -1,0 +1,236 @@
+"""Python binding of the C ABI in ``include/qlbm.h`` (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in the
+in-tree CUDA library ``_build/libqlbm.so``; all arithmetic of the lattice
+Boltzmann step runs in that library's kernels.  Arrays may be numpy arrays
+(host memory) or CUDA torch tensors (device memory of the handle's GPU);
+both must be C-contiguous float64 in the layouts the header documents.
+
+Importing this module fails loudly if the library has not been built: there
+is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+QLBM_OK = 0
+QLBM_ERR_INVALID_ARG = -1
+QLBM_ERR_UNSUPPORTED = -2
+QLBM_ERR_OOM = -3
+QLBM_ERR_CUDA = -4
+QLBM_ERR_NONFINITE = -5
+QLBM_ERR_NONPOSITIVE_DENSITY = -6
+QLBM_ERR_STATE = -7
+
+QLBM_D2Q9 = 2
+QLBM_D3Q19 = 3
+QLBM_FP64 = 0
+QLBM_FP32 = 1
+QLBM_FP16_DEV = 2
+QLBM_HOST = 0
+QLBM_DEVICE = 1
+
+PRECISIONS = {"fp64": QLBM_FP64, "fp32": QLBM_FP32, "fp16dev": QLBM_FP16_DEV}
+
+LIB_PATH = _build.LIB
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libqlbm.so is not built (%s); run __graft_entry__.build() first" % LIB_PATH)
+_lib = ctypes.CDLL(LIB_PATH)
+
+_vp = ctypes.c_void_p
+_d = ctypes.c_double
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_create = _sig("qlbm_create", _i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_i64), _d, _d, _d, _i, _vp])
+_destroy = _sig("qlbm_destroy", None, [_vp])
+_last_error = _sig("qlbm_last_error", ctypes.c_char_p, [_vp])
+_info = _sig("qlbm_info", _i, [_vp, _vp, _i])
+_init_eq = _sig("qlbm_init_equilibrium", _i, [_vp, _vp, _vp, _vp, _i])
+_step = _sig("qlbm_step", _i, [_vp, _i64])
+_time = _sig("qlbm_time", _i64, [_vp])
+_sync = _sig("qlbm_sync", _i, [_vp])
+_moments = _sig("qlbm_moments", _i, [_vp, _vp, _vp, _vp, _i])
+_conserved = _sig("qlbm_conserved", _i, [_vp, _vp])
+_get_state = _sig("qlbm_get_state", _i, [_vp, _vp, _i])
+_set_state = _sig("qlbm_set_state", _i, [_vp, _vp, _i])
+
+
+class QLBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("qlbm error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(rc, h=None):
+    if rc != QLBM_OK:
+        msg = _last_error(h)
+        raise QLBMError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a, kind=None):
+    """(pointer, ptr_kind) of a numpy array or CUDA tensor; None -> NULL."""
+    if a is None:
+        return None, kind
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, QLBM_HOST
+    # torch tensor
+    if not getattr(a, "is_cuda", False):
+        raise TypeError("expected a numpy array or a CUDA tensor")
+    import torch
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise TypeError("device tensors must be contiguous float64")
+    return a.data_ptr(), QLBM_DEVICE
+
+
+def _kind(*ptrs):
+    kinds = {k for p, k in ptrs if p is not None}
+    if len(kinds) != 1:
+        raise TypeError("all array arguments must live on the same side (host or device)")
+    return kinds.pop()
+
+
+def qlbm_create(lattice, dims, tau, beta0, dt=1.0, precision=QLBM_FP64, stream=None):
+    """Returns a handle (int); stream is a cudaStream_t value (int) or None."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    d = (ctypes.c_int64 * 3)(*[int(v) for v in (list(dims) + [1] * (3 - len(dims)))])
+    h = _vp()
+    _check(_create(ctypes.byref(h), int(lattice), d, float(tau), float(beta0), float(dt),
+                   int(precision), _vp(stream) if stream else None))
+    return h.value
+
+
+def qlbm_destroy(h):
+    _destroy(h)
+
+
+def qlbm_last_error(h=None):
+    m = _last_error(h)
+    return m.decode() if m else ""
+
+
+def qlbm_info(h):
+    out = np.zeros(16)
+    _check(_info(h, out.ctypes.data, 16), h)
+    keys = ["d", "b", "xi", "a", "w_rest", "w_axis", "w_diag", "c", "m", "alpha3", "alpha4",
+            "alpha5", "tau", "beta0", "dt", "precision"]
+    return dict(zip(keys, out.tolist()))
+
+
+def qlbm_init_equilibrium(h, rho4, u, eps=None):
+    p = [_ptr(rho4), _ptr(u), _ptr(eps)]
+    _check(_init_eq(h, p[0][0], p[1][0], p[2][0], _kind(*p)), h)
+
+
+def qlbm_step(h, nsteps):
+    _check(_step(h, int(nsteps)), h)
+
+
+def qlbm_time(h):
+    return _time(h)
+
+
+def qlbm_sync(h):
+    _check(_sync(h), h)
+
+
+def qlbm_moments(h, rho4=None, u=None, eps=None):
+    p = [_ptr(rho4), _ptr(u), _ptr(eps)]
+    _check(_moments(h, p[0][0], p[1][0], p[2][0], _kind(*p)), h)
+
+
+def qlbm_conserved(h):
+    out = np.zeros(8)
+    _check(_conserved(h, out.ctypes.data), h)
+    return out
+
+
+def qlbm_get_state(h, buf):
+    p, k = _ptr(buf)
+    _check(_get_state(h, p, k), h)
+    return buf
+
+
+def qlbm_set_state(h, buf):
+    p, k = _ptr(buf)
+    _check(_set_state(h, p, k), h)
+
+
+class Lattice:
+    """Owning wrapper of a handle with numpy conveniences (host round trips)."""
+
+    def __init__(self, lattice, dims, tau, beta0=1.0, dt=1.0, precision="fp64", stream=None):
+        if lattice in ("D2Q9", "d2q9"):
+            lattice = QLBM_D2Q9
+        elif lattice in ("D3Q19", "d3q19"):
+            lattice = QLBM_D3Q19
+        self.d = int(lattice)
+        self.b = 9 if self.d == 2 else 19
+        self.dims = tuple(int(v) for v in (list(dims) + [1] * (3 - len(dims))))
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        self.h = qlbm_create(lattice, self.dims, tau, beta0, dt, precision, stream)
+
+    def close(self):
+        if self.h:
+            qlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self):
+        return qlbm_info(self.h)
+
+    def init_equilibrium(self, rho4, u, eps=None):
+        qlbm_init_equilibrium(self.h, rho4, u, eps)
+
+    def step(self, n=1):
+        qlbm_step(self.h, n)
+
+    def time(self):
+        return qlbm_time(self.h)
+
+    def sync(self):
+        qlbm_sync(self.h)
+
+    def moments(self):
+        rho4 = np.zeros((4, self.N))
+        u = np.zeros((self.d, self.N))
+        eps = np.zeros(self.N)
+        qlbm_moments(self.h, rho4, u, eps)
+        return rho4, u, eps
+
+    def conserved(self):
+        return qlbm_conserved(self.h)
+
+    def get_state(self):
+        buf = np.zeros((self.b, 4, self.N))
+        qlbm_get_state(self.h, buf)
+        return buf
+
+    def set_state(self, state):
+        qlbm_set_state(self.h, np.ascontiguousarray(state, dtype=np.float64))

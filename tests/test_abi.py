@@ -1,0 +1,57 @@
+"""The C ABI library loads and exports every entry point that include/*.h
+declares; argument checks that run before any CUDA call behave (no GPU
+needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(qlbm_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    from paper_1309_1656_gb300 import _build
+    if not _build.up_to_date():
+        g.build()
+    return ctypes.CDLL(_build.LIB)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("qlbm_create", "qlbm_destroy", "qlbm_init_equilibrium", "qlbm_step", "qlbm_moments",
+              "qlbm_conserved", "qlbm_get_state", "qlbm_set_state", "qlbm_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    from paper_1309_1656_gb300 import qlbm
+    for kw in (dict(lattice=5, dims=(4, 4, 1)), dict(lattice=2, dims=(4, 4, 2)),
+               dict(lattice=3, dims=(0, 4, 4)), dict(lattice=2, dims=(4, 4, 1), tau=-1.0),
+               dict(lattice=2, dims=(4, 4, 1), beta0=0.0),
+               dict(lattice=2, dims=(4, 4, 1), precision=7)):
+        args = dict(tau=0.8, beta0=1.0, dt=1.0, precision=0)
+        args.update(kw)
+        with pytest.raises(qlbm.QLBMError) as e:
+            qlbm.qlbm_create(args["lattice"], args["dims"], args["tau"], args["beta0"], args["dt"],
+                             args["precision"])
+        assert e.value.code == qlbm.QLBM_ERR_INVALID_ARG
+        assert qlbm.qlbm_last_error(None)
