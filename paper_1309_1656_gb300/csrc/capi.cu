@@ -137,9 +137,6 @@ int qlbm_create(qlbm_handle *out, int lattice, const int64_t dims[3], double tau
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "lattice too large for the launch grid");
     }
     h->elem_bytes = precision == QLBM_FP64 ? 8 : (precision == QLBM_FP32 ? 4 : 2);
-    // FP16 deviation reference: the uniform equilibrium n = 1, u = 0,
-    // eps = eps0, where P_i = 1 and W_i^ref = w_i / 2 * 1, i.e. f_ref = w_i.
-    for (int i = 0; i < 3; ++i) h->fref[i] = (float)h->hc.w[i];
 
     cudaError_t e = cudaGetDevice(&h->device);
     size_t bytes = (size_t)h->b * 4 * (size_t)g.P * h->elem_bytes;

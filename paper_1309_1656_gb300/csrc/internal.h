@@ -47,7 +47,6 @@ struct qlbm_ctx {
     int nred = 0;
     double *staging = nullptr;      // device staging for host inputs/outputs
     size_t staging_bytes = 0;
-    float fref[3] = {0, 0, 0};      // FP16 deviation reference by |i|^2
     const qlbm::LatticeOps *ops = nullptr;
     std::string err;
 };

@@ -17,6 +17,8 @@
 // it is back in natural order.
 #pragma once
 
+#include <type_traits>
+
 #include "lattice.cuh"
 
 namespace qlbm {
@@ -71,11 +73,10 @@ __device__ __forceinline__ void gather(const Planes<typename Codec::S, Lattice<D
     for (int q = 0; q < Q; ++q) {
         const int p = SWAPPED ? opposite<D>(q) : q;     // population held by slot q
         const int s = SWAPPED ? neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q)) : si.s;
-        const int cls = cnorm2<D>(q);
-        f[p] = codec.load(pl.p[4 * q][s], 0, cls);
-        sx[p] = codec.load(pl.p[4 * q + 1][s], 1, cls);
-        sy[p] = codec.load(pl.p[4 * q + 2][s], 2, cls);
-        sz[p] = codec.load(pl.p[4 * q + 3][s], 3, cls);
+        f[p] = codec.load(pl.p[4 * q][s]);
+        sx[p] = codec.load(pl.p[4 * q + 1][s]);
+        sy[p] = codec.load(pl.p[4 * q + 2][s]);
+        sz[p] = codec.load(pl.p[4 * q + 3][s]);
     }
 }
 
@@ -92,7 +93,11 @@ k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typena
     if (!site_of_block(g, si)) return;
     R f[Q], sx[Q], sy[Q], sz[Q];
     gather<D, Codec, ODD>(pl, g, si, codec, f, sx, sy, sz);
-    const unsigned flag = collide<D, R>(f, sx, sy, sz, k);
+    unsigned flag;
+    if constexpr (Codec::DEV)
+        flag = collide_dev<D>(f, sx, sy, sz, k);
+    else
+        flag = collide<D, R>(f, sx, sy, sz, k);
     // g.zero is 0 at run time; adding it keeps the compiler from carrying the
     // 4b load addresses (identical to the store addresses) through the
     // collision in registers.
@@ -104,11 +109,10 @@ k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typena
         // population q goes to slot opposite(q) at x (even) or slot q at x + e_q (odd)
         const int slot = ODD ? q : opposite<D>(q);
         const int s = ODD ? neighbour(g, so, cx<D>(q), cy<D>(q), cz<D>(q)) : so.s;
-        const int cls = cnorm2<D>(q);
-        pl.p[4 * slot][s] = codec.store(f[q], 0, cls);
-        pl.p[4 * slot + 1][s] = codec.store(sx[q], 1, cls);
-        pl.p[4 * slot + 2][s] = codec.store(sy[q], 2, cls);
-        pl.p[4 * slot + 3][s] = codec.store(sz[q], 3, cls);
+        pl.p[4 * slot][s] = codec.store(f[q]);
+        pl.p[4 * slot + 1][s] = codec.store(sx[q]);
+        pl.p[4 * slot + 2][s] = codec.store(sy[q]);
+        pl.p[4 * slot + 3][s] = codec.store(sz[q]);
     }
     if (flag) atomicOr(flags, flag);
 }
@@ -121,14 +125,6 @@ struct InitConsts {
     double xi, K, c, inv_mc2, c3, c4, c5, eps0, beta0;
     double w[3];
 };
-
-template <class Codec> __device__ __forceinline__ typename Codec::S store_from_double(const Codec &, double v, int, int);
-template <> __device__ __forceinline__ double store_from_double(const CodecF64 &, double v, int, int) { return v; }
-template <> __device__ __forceinline__ float store_from_double(const CodecF32 &, double v, int, int) { return (float)v; }
-template <> __device__ __forceinline__ __half store_from_double(const CodecF16Dev &c, double v, int comp, int cls)
-{
-    return __double2half(comp == 0 ? v - (double)c.fref[cls] : v);
-}
 
 template <int D>
 __device__ __forceinline__ double poly_P_d(const InitConsts &ic, int q, double jx, double jy, double jz, double be)
@@ -158,10 +154,10 @@ k_init_eq(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, InitConsts 
     for (int q = 0; q < Q; ++q) {
         const int cls = cnorm2<D>(q);
         const double wp = ic.w[cls] * poly_P_d<D>(ic, q, jx, jy, jz, be);
-        pl.p[4 * q][s] = store_from_double(codec, wp * n, 0, cls);
-        pl.p[4 * q + 1][s] = store_from_double(codec, wp * Sx, 1, cls);
-        pl.p[4 * q + 2][s] = store_from_double(codec, wp * Sy, 2, cls);
-        pl.p[4 * q + 3][s] = store_from_double(codec, wp * Sz, 3, cls);
+        pl.p[4 * q][s] = codec.from_double(wp * n, 0, cls);
+        pl.p[4 * q + 1][s] = codec.from_double(wp * Sx, 1, cls);
+        pl.p[4 * q + 2][s] = codec.from_double(wp * Sy, 2, cls);
+        pl.p[4 * q + 3][s] = codec.from_double(wp * Sz, 3, cls);
     }
 }
 
@@ -182,10 +178,11 @@ k_get_state(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec cod
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         double *o = out + (int64_t)(4 * q) * N + si.s;
-        o[0] = (double)f[q];
-        o[N] = (double)sx[q];
-        o[2 * N] = (double)sy[q];
-        o[3 * N] = (double)sz[q];
+        const int cls = cnorm2<D>(q);
+        o[0] = codec.to_double(f[q], 0, cls);
+        o[N] = codec.to_double(sx[q], 1, cls);
+        o[2 * N] = codec.to_double(sy[q], 2, cls);
+        o[3 * N] = codec.to_double(sz[q], 3, cls);
     }
 }
 
@@ -202,7 +199,7 @@ k_set_state(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec cod
         const double *v = in + (int64_t)(4 * q) * N + si.s;
         const int cls = cnorm2<D>(q);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) pl.p[4 * q + c][si.s] = store_from_double(codec, v[c * N], c, cls);
+        for (int c = 0; c < 4; ++c) pl.p[4 * q + c][si.s] = codec.from_double(v[c * N], c, cls);
     }
 }
 
@@ -223,10 +220,11 @@ k_moments(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec codec
     double fd[Q], xd[Q], yd[Q], zd[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        fd[q] = f[q];
-        xd[q] = sx[q];
-        yd[q] = sy[q];
-        zd[q] = sz[q];
+        const int cls = cnorm2<D>(q);
+        fd[q] = codec.to_double(f[q], 0, cls);
+        xd[q] = codec.to_double(sx[q], 1, cls);
+        yd[q] = codec.to_double(sy[q], 2, cls);
+        zd[q] = codec.to_double(sz[q], 3, cls);
     }
     const SiteMoments<D, double> m = site_moments<D, double>(fd, xd, yd, zd);
     const int64_t N = g.N, s = si.s;
@@ -288,11 +286,12 @@ k_conserved_partial(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, C
         gather<D, Codec, SWAPPED>(pl, g, si, codec, f, sx, sy, sz);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const double fq = f[q];
+            const int cls = cnorm2<D>(q);
+            const double fq = codec.to_double(f[q], 0, cls);
             acc[0] += fq;
-            acc[1] += (double)sx[q];
-            acc[2] += (double)sy[q];
-            acc[3] += (double)sz[q];
+            acc[1] += codec.to_double(sx[q], 1, cls);
+            acc[2] += codec.to_double(sy[q], 2, cls);
+            acc[3] += codec.to_double(sz[q], 3, cls);
             acc[4] += cx<D>(q) * fq;
             acc[5] += cy<D>(q) * fq;
             acc[6] += cz<D>(q) * fq;

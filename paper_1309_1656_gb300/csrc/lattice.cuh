@@ -44,13 +44,17 @@ template <int D> __host__ __device__ constexpr int opposite(int q) { return Latt
 //   alpha2 = (beta0 eps - c)/(m - c^2),      alpha1 = 1 - c alpha2,
 //   P_i = alpha1 + alpha2 K |i|^2 + c3 (i.j) + c4 (i.j)^2 + c5 |j|^2,
 // with c3 = 2K alpha3, c4 = 4K^2 alpha4, c5 = K alpha5 (Eq. WeqAlgo).
+// g00, g01, g11 invert the Gram matrix of (1, |i|^2) under the weights and
+// gj = 1 / sum_i w_i i_x^2; they project rounding residuals out of the
+// single-precision equilibrium (see collide).
 template <typename R> struct Coll {
     R K, c, inv_mc2;
     R c3, c4, c5;
-    R omega, omc;   // dt/tau and 1 - dt/tau
-    R ow[3];        // omega * w for |i|^2 = 0, 1, 2
+    R omega;        // dt/tau
+    R w[3];         // weights for |i|^2 = 0, 1, 2
+    R g00, g01, g11, gj;
+    R S2;           // sum_i w_i |i|^2 (= c / K)
 };
-
 // Bits of the device flag word.
 enum : unsigned { FLAG_NONFINITE = 1u, FLAG_NONPOSITIVE = 2u };
 
@@ -99,8 +103,10 @@ __device__ __forceinline__ SiteMoments<D, R> site_moments(const R *f, const R *s
     return m;
 }
 
-// Fused equilibrium + BGK relaxation of one site, in place on the Pauli
-// components (Eqs. WeqAlgo and CollisionStep).  Returns flag bits.
+// Fused equilibrium + BGK relaxation of one site on populations held as
+// they are (double precision path), in place on the Pauli components:
+// Eq. WeqAlgo and Eq. CollisionStep in the paper's form W' = W + omega (W^eq - W).
+// Returns flag bits.
 template <int D, typename R>
 __device__ __forceinline__ unsigned collide(R *f, R *sx, R *sy, R *sz, const Coll<R> &k)
 {
@@ -115,19 +121,12 @@ __device__ __forceinline__ unsigned collide(R *f, R *sx, R *sy, R *sz, const Col
     const R bq[3] = {b0, b0 + a2K, b0 + R(2) * a2K};
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        R t = R(0);
-        if (cx<D>(q) > 0) t += m.jx;
-        if (cx<D>(q) < 0) t -= m.jx;
-        if (cy<D>(q) > 0) t += m.jy;
-        if (cy<D>(q) < 0) t -= m.jy;
-        if (cz<D>(q) > 0) t += m.jz;
-        if (cz<D>(q) < 0) t -= m.jz;
-        const R P = fmadd(t, fmadd(k.c4, t, k.c3), bq[cnorm2<D>(q)]);
-        const R g = k.ow[cnorm2<D>(q)] * P;
-        f[q] = fmadd(g, m.n, k.omc * f[q]);
-        sx[q] = fmadd(g, m.Sx, k.omc * sx[q]);
-        sy[q] = fmadd(g, m.Sy, k.omc * sy[q]);
-        sz[q] = fmadd(g, m.Sz, k.omc * sz[q]);
+        const R t = cx<D>(q) * m.jx + cy<D>(q) * m.jy + cz<D>(q) * m.jz;
+        const R h = k.w[cnorm2<D>(q)] * fmadd(t, fmadd(k.c4, t, k.c3), bq[cnorm2<D>(q)]);
+        f[q] = fmadd(k.omega, fmadd(h, m.n, -f[q]), f[q]);
+        sx[q] = fmadd(k.omega, fmadd(h, m.Sx, -sx[q]), sx[q]);
+        sy[q] = fmadd(k.omega, fmadd(h, m.Sy, -sy[q]), sy[q]);
+        sz[q] = fmadd(k.omega, fmadd(h, m.Sz, -sz[q]), sz[q]);
     }
     unsigned flag = 0u;
     if (!(m.n > R(0))) flag |= (m.n == m.n) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;
@@ -135,33 +134,157 @@ __device__ __forceinline__ unsigned collide(R *f, R *sx, R *sy, R *sz, const Col
     return flag;
 }
 
-// Storage codecs: how a stored value becomes an arithmetic value and back.
+// The same collision in single precision on deviations from the uniform
+// reference equilibrium (n = 1, S = 0, u = 0, eps = eps0, where P_i = 1):
+// d_i = f_i - w_i and s_i as they are.  Every quantity formed is a small
+// fluctuation, so no digits are lost to cancellation:
+//   n = 1 + dn, dn = sum d_i;   j = J/n, J = sum i d_i   (sum w_i i = 0);
+//   E2/n = S2 + de, de = (dE - S2 dn)/n, dE = sum |i|^2 d_i, S2 = sum w_i |i|^2;
+//   beta0 eps - c = K (de - |j|^2)                       (c = K S2);
+//   P_i - 1 = -c alpha2 + alpha2 K |i|^2 + c3 t + c4 t^2 + c5 |j|^2, t = i.j;
+//   g_i = f_i^eq - w_i = w_i ((P_i - 1) n + dn),   s_i^eq = w_i P_i S.
+// Exact moments: in exact arithmetic sum g_i = dn, sum g_i i = J and
+// sum g_i |i|^2 = dE (Sec. 3.2), so the collision conserves mass, momentum
+// and energy.  Rounded constants make these sums miss by ~1e-8..1e-7 in the
+// same direction at every site and step (a drift of ~1e-5 over 1000
+// steps).  A first pass measures the residuals of g against the moments of
+// the inputs and removes them by the weighted least-change correction
+// g_i -= w_i (A + B.i + C |i|^2) (which only shifts the base coefficients
+// and adds one linear term); the rest population then takes the exact mass
+// and spin balance.  What remains is unbiased rounding.
+template <int D>
+__device__ __forceinline__ unsigned collide_dev(float *d, float *sx, float *sy, float *sz,
+                                                const Coll<float> &k)
+{
+    constexpr int Q = Lattice<D>::Q;
+    constexpr int REST = (Q - 1) / 2;
+    float dn = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f;
+    float jxp = 0.f, jxm = 0.f, jyp = 0.f, jym = 0.f, jzp = 0.f, jzm = 0.f, e1 = 0.f, e2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        dn += d[q];
+        Sx += sx[q];
+        Sy += sy[q];
+        Sz += sz[q];
+        if (cx<D>(q) > 0) jxp += d[q];
+        if (cx<D>(q) < 0) jxm += d[q];
+        if (cy<D>(q) > 0) jyp += d[q];
+        if (cy<D>(q) < 0) jym += d[q];
+        if (cz<D>(q) > 0) jzp += d[q];
+        if (cz<D>(q) < 0) jzm += d[q];
+        if (cnorm2<D>(q) == 1) e1 += d[q];
+        if (cnorm2<D>(q) == 2) e2 += d[q];
+    }
+    const float n = 1.f + dn;
+    const float rn = 1.f / n;
+    const float Jx = jxp - jxm, Jy = jyp - jym, Jz = (D == 3) ? jzp - jzm : 0.f;
+    const float dE = e1 + 2.f * e2;
+    const float jx = Jx * rn, jy = Jy * rn, jz = Jz * rn;
+    const float de = fmaf(-k.S2, dn, dE) * rn;
+    const float jj = jx * jx + jy * jy + jz * jz;
+    const float a2 = k.K * (de - jj) * k.inv_mc2;          // alpha2
+    const float a2K = a2 * k.K;
+    const float p0 = fmaf(k.c5, jj, -k.c * a2);            // alpha1 - 1 + alpha5 K |j|^2
+    float bq[3] = {p0, p0 + a2K, p0 + 2.f * a2K};
+    // residual pass
+    float s0 = 0.f, s2 = 0.f, sxp = 0.f, syp = 0.f, szp = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const float t = cx<D>(q) * jx + cy<D>(q) * jy + cz<D>(q) * jz;
+        const float P1 = fmaf(t, fmaf(k.c4, t, k.c3), bq[cnorm2<D>(q)]);
+        const float g = k.w[cnorm2<D>(q)] * fmaf(P1, n, dn);
+        s0 += g;
+        if (cnorm2<D>(q) == 1) s2 += g;
+        if (cnorm2<D>(q) == 2) s2 += 2.f * g;
+        if (cx<D>(q) > 0) sxp += g;
+        if (cx<D>(q) < 0) sxp -= g;
+        if (cy<D>(q) > 0) syp += g;
+        if (cy<D>(q) < 0) syp -= g;
+        if (cz<D>(q) > 0) szp += g;
+        if (cz<D>(q) < 0) szp -= g;
+    }
+    const float r0 = s0 - dn, r2 = s2 - dE;
+    const float A = (k.g00 * r0 + k.g01 * r2) * rn;
+    const float C = (k.g01 * r0 + k.g11 * r2) * rn;
+    const float Bx = (sxp - Jx) * k.gj * rn, By = (syp - Jy) * k.gj * rn;
+    const float Bz = (D == 3) ? (szp - Jz) * k.gj * rn : 0.f;
+    bq[0] -= A;
+    bq[1] -= A + C;
+    bq[2] -= A + 2.f * C;
+    float dr = 0.f, xr = 0.f, yr = 0.f, zr = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const float t = cx<D>(q) * jx + cy<D>(q) * jy + cz<D>(q) * jz;
+        const float w = k.w[cnorm2<D>(q)];
+        const float P1 = fmaf(t, fmaf(k.c4, t, k.c3), bq[cnorm2<D>(q)]) -
+                         (cx<D>(q) * Bx + cy<D>(q) * By + cz<D>(q) * Bz);
+        const float g = w * fmaf(P1, n, dn);          // f_i^eq - w_i
+        const float hp = fmaf(w, P1, w);              // w_i P_i
+        d[q] = fmaf(k.omega, g - d[q], d[q]);
+        sx[q] = fmaf(k.omega, fmaf(hp, Sx, -sx[q]), sx[q]);
+        sy[q] = fmaf(k.omega, fmaf(hp, Sy, -sy[q]), sy[q]);
+        sz[q] = fmaf(k.omega, fmaf(hp, Sz, -sz[q]), sz[q]);
+        if (q != REST) {
+            dr += d[q];
+            xr += sx[q];
+            yr += sy[q];
+            zr += sz[q];
+        }
+    }
+    d[REST] = dn - dr;
+    sx[REST] = Sx - xr;
+    sy[REST] = Sy - yr;
+    sz[REST] = Sz - zr;
+    unsigned flag = 0u;
+    if (!(n > 0.f)) flag |= (n == n) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;
+    if (!(fabsf(Sx) + fabsf(Sy) + fabsf(Sz) + fabsf(de) < 1e30f)) flag |= FLAG_NONFINITE;
+    return flag;
+}
+
+// Storage codecs: the stored type S, the arithmetic type R, and whether
+// the kernels work on deviations d_i = f_i - w_i (DEV) or on f_i itself.
+// to_double / from_double convert a stored value of component comp (0 = f,
+// 1..3 = s) of a direction of class cls = |i|^2 to and from the value of
+// the population itself, in double.
 struct CodecF64 {
     using S = double;
     using R = double;
-    __device__ __forceinline__ R load(S v, int, int) const { return v; }
-    __device__ __forceinline__ S store(R v, int, int) const { return v; }
+    static constexpr bool DEV = false;
+    __device__ __forceinline__ R load(S v) const { return v; }
+    __device__ __forceinline__ S store(R v) const { return v; }
+    __device__ __forceinline__ double to_double(R v, int, int) const { return v; }
+    __device__ __forceinline__ S from_double(double v, int, int) const { return v; }
 };
 struct CodecF32 {
     using S = float;
     using R = float;
-    __device__ __forceinline__ R load(S v, int, int) const { return v; }
-    __device__ __forceinline__ S store(R v, int, int) const { return v; }
+    static constexpr bool DEV = true;
+    double fref[3];   // w_i by class: the reference equilibrium's traces
+    __device__ __forceinline__ R load(S v) const { return v; }
+    __device__ __forceinline__ S store(R v) const { return v; }
+    __device__ __forceinline__ double to_double(R v, int comp, int cls) const
+    {
+        return comp == 0 ? fref[cls] + (double)v : (double)v;
+    }
+    __device__ __forceinline__ S from_double(double v, int comp, int cls) const
+    {
+        return (float)(comp == 0 ? v - fref[cls] : v);
+    }
 };
-// Half-precision deviation from a uniform reference equilibrium: the trace
-// component stores f_i - fref[|i|^2], the spin components (reference 0) are
-// stored as they are.
 struct CodecF16Dev {
     using S = __half;
     using R = float;
-    float fref[3];
-    __device__ __forceinline__ R load(S v, int comp, int cls) const
+    static constexpr bool DEV = true;
+    double fref[3];
+    __device__ __forceinline__ R load(S v) const { return __half2float(v); }
+    __device__ __forceinline__ S store(R v) const { return __float2half_rn(v); }
+    __device__ __forceinline__ double to_double(R v, int comp, int cls) const
     {
-        return comp == 0 ? fref[cls] + __half2float(v) : __half2float(v);
+        return comp == 0 ? fref[cls] + (double)v : (double)v;
     }
-    __device__ __forceinline__ S store(R v, int comp, int cls) const
+    __device__ __forceinline__ S from_double(double v, int comp, int cls) const
     {
-        return __float2half_rn(comp == 0 ? v - fref[cls] : v);
+        return __double2half(comp == 0 ? v - fref[cls] : v);
     }
 };
 

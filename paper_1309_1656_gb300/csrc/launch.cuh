@@ -20,8 +20,20 @@ template <typename R> Coll<R> make_coll(const qlbm_ctx *h)
     c.c4 = (R)(4.0 * k.K * k.K * k.alpha4);
     c.c5 = (R)(k.K * k.alpha5);
     c.omega = (R)omega;
-    c.omc = (R)(1.0 - omega);
-    for (int i = 0; i < 3; ++i) c.ow[i] = (R)(omega * k.w[i]);
+    for (int i = 0; i < 3; ++i) c.w[i] = (R)k.w[i];
+    // Gram matrix of (1, |i|^2) under the weights, and sum w i_x^2
+    const int d = k.d;
+    const double na = (d == 2) ? 4.0 : 6.0, nd = (d == 2) ? 4.0 : 12.0;  // axis / diagonal counts
+    const double S0 = k.w[0] + na * k.w[1] + nd * k.w[2];
+    const double S2 = na * k.w[1] + 2.0 * nd * k.w[2];
+    const double S4 = na * k.w[1] + 4.0 * nd * k.w[2];
+    const double det = S0 * S4 - S2 * S2;
+    c.g00 = (R)(S4 / det);
+    c.g01 = (R)(-S2 / det);
+    c.g11 = (R)(S0 / det);
+    const double sx2 = 2.0 * k.w[1] + ((d == 2) ? 4.0 : 8.0) * k.w[2];
+    c.gj = (R)(1.0 / sx2);
+    c.S2 = (R)S2;
     return c;
 }
 
@@ -44,11 +56,18 @@ inline InitConsts make_init(const qlbm_ctx *h)
 
 template <class Codec> Codec make_codec(const qlbm_ctx *h);
 template <> inline CodecF64 make_codec<CodecF64>(const qlbm_ctx *) { return CodecF64{}; }
-template <> inline CodecF32 make_codec<CodecF32>(const qlbm_ctx *) { return CodecF32{}; }
+// Deviation reference: the uniform equilibrium n = 1, S = 0, u = 0,
+// eps = eps0, where P_i = 1, so f_i^ref = w_i and s_i^ref = 0.
+template <> inline CodecF32 make_codec<CodecF32>(const qlbm_ctx *h)
+{
+    CodecF32 c;
+    for (int i = 0; i < 3; ++i) c.fref[i] = h->hc.w[i];
+    return c;
+}
 template <> inline CodecF16Dev make_codec<CodecF16Dev>(const qlbm_ctx *h)
 {
     CodecF16Dev c;
-    for (int i = 0; i < 3; ++i) c.fref[i] = h->fref[i];
+    for (int i = 0; i < 3; ++i) c.fref[i] = h->hc.w[i];
     return c;
 }
 

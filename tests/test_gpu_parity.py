@@ -79,17 +79,43 @@ def test_default_eps_is_eps0(q, oracle_mod):
             assert np.allclose(e, oracle_mod.eps0(d, 1.3), rtol=1e-13)
 
 
-@pytest.mark.parametrize("d,dims,prec", [(2, (37, 29, 1), "fp64"), (3, (9, 7, 5), "fp64"),
-                                         (2, (37, 29, 1), "fp32"), (3, (9, 7, 5), "fp32")])
-def test_conservation_drift(q, d, dims, prec):
-    st = fields.random_populations(d, dims, seed=5)
+DRIFT_CASES = [(2, (128, 96, 1), "fp64"), (3, (32, 24, 20), "fp64"),
+               (2, (128, 96, 1), "fp32"), (3, (32, 24, 20), "fp32")]
+
+
+def _drift(q, d, dims, prec, state=None, fl=None, nsteps=100):
     with q.Lattice(d, dims, 0.6, 1.0, precision=prec) as lat:
-        lat.set_state(st)
+        if state is not None:
+            lat.set_state(state)
+        else:
+            lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
         c0 = lat.conserved()
-        lat.step(100)
+        lat.step(nsteps)
         c1 = lat.conserved()
-    tol = 1e-13 if prec == "fp64" else 2e-6
-    assert np.max(np.abs(c1 - c0)) <= tol * np.max(np.abs(c0))
+    return float(np.max(np.abs(c1 - c0)) / np.max(np.abs(c0)))
+
+
+@pytest.mark.parametrize("d,dims,prec", DRIFT_CASES)
+def test_conservation_drift_near_equilibrium(q, d, dims, prec):
+    # Eqs. GlobalDensity/GlobalVelocity/GlobalTotalEnergy over 100 steps of
+    # paper-shaped Fourier-mode fields (flow develops, collisions active).
+    # Single precision leaves an unbiased random walk of roundings of
+    # ~1e-9 here; a biased equilibrium moment (rounded constants) would
+    # drift by ~1e-7 per step, i.e. >= 1e-5.
+    fl = fields.modes(d, dims, seed=8, amp=0.05, umax=0.1)
+    tol = 1e-13 if prec == "fp64" else 2e-8
+    assert _drift(q, d, dims, prec, fl=fl) <= tol
+
+
+@pytest.mark.parametrize("d,dims,prec", DRIFT_CASES)
+def test_conservation_drift_far_from_equilibrium(q, d, dims, prec):
+    # Random populations (n ~ 2, far from the n = 1 deviation reference,
+    # strongly non-equilibrium): single-precision rounding is then of the
+    # order of the values themselves; the bound allows a bias of at most
+    # 0.1 ulp per site and step (1e-6 over 100 steps).
+    st = fields.random_populations(d, dims, seed=5)
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    assert _drift(q, d, dims, prec, state=st) <= tol
 
 
 @pytest.mark.parametrize("d,dims,tau", [(2, (64, 64, 1), 0.8), (3, (24, 20, 16), 0.7)])
