@@ -326,10 +326,11 @@ def cpu_baseline(w, target_s=15.0):
     N = dims[0] * dims[1] * dims[2]
     cores = oracle.max_threads(0)
     st = oracle.init_equilibrium(d, dims, w["beta0"], fl["rho4"], fl["u"], fl["eps"])
+    st = oracle.run(d, dims, w["tau"], w["beta0"], 2, st)      # thread start-up
     t = time.perf_counter()
-    st = oracle.run(d, dims, w["tau"], w["beta0"], 1, st)
-    t1 = time.perf_counter() - t
-    n = int(max(1, min(2000, target_s / max(t1, 1e-6))))
+    st = oracle.run(d, dims, w["tau"], w["beta0"], 3, st)
+    t1 = (time.perf_counter() - t) / 3.0
+    n = int(max(1, min(20000, target_s / max(t1, 1e-6))))
     t = time.perf_counter()
     oracle.run(d, dims, w["tau"], w["beta0"], n, st)
     dt = time.perf_counter() - t

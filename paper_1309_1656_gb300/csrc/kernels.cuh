@@ -83,7 +83,7 @@ __device__ __forceinline__ void gather(const Planes<typename Codec::S, Lattice<D
 // One AA step (even: ODD = false, odd: ODD = true), fused
 // moments + equilibrium + collision + streaming.
 template <int D, class Codec, bool ODD>
-__global__ void __launch_bounds__(kStepBlock)
+__global__ void __launch_bounds__(kStepBlock, Codec::MIN_BLOCKS)
 k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typename Codec::R> k,
           Codec codec, unsigned *__restrict__ flags)
 {

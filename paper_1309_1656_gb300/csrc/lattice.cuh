@@ -241,8 +241,9 @@ __device__ __forceinline__ unsigned collide_dev(float *d, float *sx, float *sy, 
     return flag;
 }
 
-// Storage codecs: the stored type S, the arithmetic type R, and whether
-// the kernels work on deviations d_i = f_i - w_i (DEV) or on f_i itself.
+// Storage codecs: the stored type S, the arithmetic type R, whether the
+// kernels work on deviations d_i = f_i - w_i (DEV) or on f_i itself, and
+// the step kernel's minimum resident blocks per SM (register budget).
 // to_double / from_double convert a stored value of component comp (0 = f,
 // 1..3 = s) of a direction of class cls = |i|^2 to and from the value of
 // the population itself, in double.
@@ -250,6 +251,7 @@ struct CodecF64 {
     using S = double;
     using R = double;
     static constexpr bool DEV = false;
+    static constexpr int MIN_BLOCKS = 1;   // 76 doubles per site need the registers
     __device__ __forceinline__ R load(S v) const { return v; }
     __device__ __forceinline__ S store(R v) const { return v; }
     __device__ __forceinline__ double to_double(R v, int, int) const { return v; }
@@ -259,6 +261,7 @@ struct CodecF32 {
     using S = float;
     using R = float;
     static constexpr bool DEV = true;
+    static constexpr int MIN_BLOCKS = 4;   // <= 128 registers: 16 warps per SM
     double fref[3];   // w_i by class: the reference equilibrium's traces
     __device__ __forceinline__ R load(S v) const { return v; }
     __device__ __forceinline__ S store(R v) const { return v; }
@@ -275,6 +278,7 @@ struct CodecF16Dev {
     using S = __half;
     using R = float;
     static constexpr bool DEV = true;
+    static constexpr int MIN_BLOCKS = 4;
     double fref[3];
     __device__ __forceinline__ R load(S v) const { return __half2float(v); }
     __device__ __forceinline__ S store(R v) const { return __float2half_rn(v); }
