@@ -154,6 +154,39 @@ int qlbm_conserved(qlbm_handle h, double *out);
 int qlbm_get_state(qlbm_handle h, double *buf, int ptr_kind);
 int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
 
+/* qlbm_conserved_static -- the same eight averages as qlbm_conserved, for a
+ * caller-owned state, without allocating any device memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate
+ * at the point of the call -- code running under another component's memory
+ * manager (a framework's caching allocator or a fixed arena that owns the
+ * device's memory) and latency-critical loops that cannot afford
+ * cudaMalloc/cudaFree, which may synchronise the whole device.
+ *   lattice  QLBM_D2Q9 or QLBM_D3Q19
+ *   dims     {nx, ny, nz} (nz = 1 for D2Q9); at most QLBM_STATIC_MAX_SITES
+ *            sites in total, else QLBM_ERR_INVALID_ARG
+ *   beta0    reference inverse temperature (fixes xi for the momentum and
+ *            energy scaling)
+ *   state    device, canonical layout double [b][4][N] (as qlbm_get_state
+ *            writes it), read only
+ *   out      device, 8 doubles, written: out[0..3] density matrix (Pauli),
+ *            out[4..6] momentum, out[7] total energy, lattice averages
+ *   stream   cudaStream_t or NULL; the call is asynchronous on it
+ * Scratch: the partial sums live in one file-scope __device__ array of
+ * QLBM_STATIC_SCRATCH_BLOCKS x 8 doubles (64 KiB) that every GPU loading the
+ * library holds until the process exits.  All calls on a device share it and
+ * it keeps the last call's contents (each call overwrites every row it
+ * reads, so nothing needs clearing); calls whose kernels overlap on the GPU
+ * (different streams, or different host threads) race on it and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  No cudaMalloc, cudaFree
+ * or allocating library routine is called.  Errors: QLBM_ERR_INVALID_ARG,
+ * QLBM_ERR_CUDA; message via qlbm_last_error(NULL). */
+#define QLBM_STATIC_SCRATCH_BLOCKS 1024
+#define QLBM_STATIC_MAX_SITES 2147483647LL
+int qlbm_conserved_static(int lattice, const int64_t dims[3], double beta0, const double *state,
+                          double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,8 @@ bool valid(qlbm_ctx *h) { return h != nullptr && h->pop != nullptr; }
 
 namespace qlbm {
 
+int set_global_error(int code, const char *msg) { return fail(nullptr, code, msg); }
+
 __global__ void __launch_bounds__(kRedBlock)
 k_conserved_final(const double *__restrict__ partials, int nparts, double xi, int64_t N,
                   double *__restrict__ out)

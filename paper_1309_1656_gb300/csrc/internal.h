@@ -67,6 +67,10 @@ const LatticeOps *lattice_ops_d3q19(int prec);
 
 cudaError_t launch_conserved_final(qlbm_ctx *h);
 
+// Records the message returned by qlbm_last_error(NULL) for calls that have
+// no handle; returns code.
+int set_global_error(int code, const char *msg);
+
 // Launch shape of the per-site kernels: one thread per site, blocks of up to
 // kStepBlock consecutive x in one row.
 inline dim3 site_block(const Grid &g)

@@ -65,6 +65,7 @@ _moments = _sig("qlbm_moments", _i, [_vp, _vp, _vp, _vp, _i])
 _conserved = _sig("qlbm_conserved", _i, [_vp, _vp])
 _get_state = _sig("qlbm_get_state", _i, [_vp, _vp, _i])
 _set_state = _sig("qlbm_set_state", _i, [_vp, _vp, _i])
+_conserved_static = _sig("qlbm_conserved_static", _i, [_i, ctypes.POINTER(_i64), _d, _vp, _vp, _vp])
 
 
 class QLBMError(RuntimeError):
@@ -169,6 +170,25 @@ def qlbm_get_state(h, buf):
 def qlbm_set_state(h, buf):
     p, k = _ptr(buf)
     _check(_set_state(h, p, k), h)
+
+
+def qlbm_conserved_static(lattice, dims, beta0, state, out, stream=None):
+    """The eight global averages of qlbm_conserved for a caller-owned device
+    state (canonical layout [b][4][N], float64) into a caller-owned device
+    buffer of 8 float64, without allocating device memory.
+
+    For callers that cannot allocate at the point of the call, e.g. code
+    running under another component's memory manager that owns the device's
+    memory, or latency-critical loops that cannot afford cudaMalloc/cudaFree.
+    The scratch is a fixed array inside the library; calls that overlap on
+    the GPU race on it.  Asynchronous on ``stream`` (a cudaStream_t value).
+    """
+    d = (ctypes.c_int64 * 3)(*[int(v) for v in (list(dims) + [1] * (3 - len(dims)))])
+    sp, sk = _ptr(state)
+    op, ok = _ptr(out)
+    if sk != QLBM_DEVICE or ok != QLBM_DEVICE:
+        raise TypeError("state and out must be CUDA tensors")
+    _check(_conserved_static(int(lattice), d, float(beta0), sp, op, _vp(stream) if stream else None))
 
 
 class Lattice:
