@@ -154,6 +154,53 @@ int qlbm_conserved(qlbm_handle h, double *out);
 int qlbm_get_state(qlbm_handle h, double *buf, int ptr_kind);
 int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
 
+/* ------------------------------------------------------------------------
+ * Reverse mode.  The gradient of an observable J of the state is carried as
+ * a cotangent lambda = dJ/dW in the canonical layout double [b][4][N]: for
+ * each population, (dJ/df, dJ/ds_x, dJ/ds_y, dJ/ds_z) of its Pauli
+ * components.  The step of Sec. 3.3 (Eqs. DiscrAvr, WeqAlgo, CollisionStep,
+ * TransportStep) is differentiated exactly by the chain rule; streaming is a
+ * permutation, so its adjoint pulls lambda_i(x + e_i).  dJ/dtau follows from
+ * omega = dt/tau in Eq. CollisionStep.  Single-precision handles carry the
+ * cotangents in float internally.
+ * ---------------------------------------------------------------------- */
+
+/* qlbm_step_adjoint -- one reverse step at the handle's current state W^n:
+ * from lam_next = dJ/dW^{n+1} returns lam = dJ/dW^n and (if dJ_dtau is not
+ * NULL) this step's contribution to dJ/dtau.  The state is not changed.
+ * lam_next and lam: [b][4][N], both host or both device (ptr_kind).
+ * Synchronising. */
+int qlbm_step_adjoint(qlbm_handle h, const double *lam_next, double *lam, double *dJ_dtau,
+                      int ptr_kind);
+
+/* qlbm_rollout -- nsteps forward steps (as qlbm_step) that also keep, in
+ * library-owned device memory, a copy of the state every `interval` steps
+ * (0: ceil(sqrt(nsteps)), the square-root checkpointing schedule) for
+ * qlbm_rollout_adjoint.  Memory: ceil(nsteps/interval) + interval - 1 state
+ * copies; QLBM_ERR_OOM (nothing run) if they do not fit.  A later step,
+ * init or set_state discards the record. */
+int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval);
+
+/* qlbm_rollout_adjoint -- reverse sweep over the last qlbm_rollout: for each
+ * checkpoint segment, last first, recompute the segment's states from its
+ * checkpoint (two-buffer forward steps), then apply the reverse step to them
+ * in reverse order.  lam_T = dJ/dW at the end of the rollout, lam_0 =
+ * dJ/dW at its start, *dJ_dtau (if not NULL) = the whole rollout's dJ/dtau.
+ * The live state (the rollout's end state) is left unchanged.  Errors:
+ * QLBM_ERR_STATE if no rollout is recorded.  Synchronising. */
+int qlbm_rollout_adjoint(qlbm_handle h, const double *lam_T, double *lam_0, double *dJ_dtau,
+                         int ptr_kind);
+
+/* qlbm_init_equilibrium_adjoint -- gradients through the initial state of
+ * qlbm_init_equilibrium (W_i = w_i P_i(u, eps) rho, Eq. WeqAlgo with u and
+ * eps given): from lam0 = dJ/dW^0 and the same (rho4, u, eps) (eps may be
+ * NULL = eps0), writes g_rho4 = dJ/drho4 [4][N], g_u = dJ/du [d][N] and
+ * g_eps = dJ/deps [N] (any output may be NULL).  All arrays on the same side
+ * (ptr_kind).  Synchronising. */
+int qlbm_init_equilibrium_adjoint(qlbm_handle h, const double *rho4, const double *u,
+                                  const double *eps, const double *lam0, double *g_rho4,
+                                  double *g_u, double *g_eps, int ptr_kind);
+
 /* qlbm_conserved_static -- the same eight averages as qlbm_conserved, for a
  * caller-owned state, without allocating any device memory.  The paper has
  * no counterpart: this entry point exists for callers that cannot allocate

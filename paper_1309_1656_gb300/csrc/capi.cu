@@ -65,6 +65,83 @@ int check_flags(qlbm_ctx *h)
 
 bool valid(qlbm_ctx *h) { return h != nullptr && h->pop != nullptr; }
 
+int64_t site_blocks(const qlbm_ctx *h) { return (int64_t)h->g.nxb * h->g.ny * h->g.nz; }
+
+int ensure_reverse(qlbm_ctx *h)
+{
+    for (int i = 0; i < 2; ++i)
+        if (!h->lam[i]) CK(h, cudaMalloc(&h->lam[i], h->lam_bytes()));
+    if (!h->dtau_acc) CK(h, cudaMalloc(&h->dtau_acc, (size_t)site_blocks(h) * sizeof(double)));
+    return QLBM_OK;
+}
+
+void free_rollout(qlbm_ctx *h)
+{
+    if (h->ck) cudaFree(h->ck);
+    if (h->seg) cudaFree(h->seg);
+    h->ck = h->seg = nullptr;
+    h->ck_slots = h->seg_slots = 0;
+    h->ro_steps = -1;
+}
+
+}  // namespace
+
+namespace qlbm {
+
+// Sum of n doubles in a fixed order (one block), scaled by `scale`.
+__global__ void __launch_bounds__(kRedBlock) k_sum_scaled(const double *__restrict__ a, int64_t n, double scale,
+                                                          double *__restrict__ out)
+{
+    double acc[1] = {0.0};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc[0] += a[i];
+    __shared__ double res[1];
+    block_sum_store<1>(acc, res);
+    __syncthreads();
+    if (threadIdx.x == 0) out[0] = res[0] * scale;
+}
+
+}  // namespace qlbm
+
+namespace {
+
+// dJ/dtau = (d omega/d tau) * sum of the per-block accumulators.
+int read_dtau(qlbm_ctx *h, double *out)
+{
+    const double domega_dtau = -h->dt / (h->tau * h->tau);
+    k_sum_scaled<<<1, kRedBlock, 0, h->stream>>>(h->dtau_acc, site_blocks(h), domega_dtau, h->red_out);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(out, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return QLBM_OK;
+}
+
+int import_lam(qlbm_ctx *h, const double *in, int ptr_kind, void *lam)
+{
+    const size_t bytes = (size_t)h->b * 4 * (size_t)h->g.N * sizeof(double);
+    if (ptr_kind == QLBM_HOST) {
+        int rc = ensure_staging(h, bytes);
+        if (rc) return rc;
+        CK(h, cudaMemcpyAsync(h->staging, in, bytes, cudaMemcpyHostToDevice, h->stream));
+        CK(h, h->ops->lam_import(h, h->staging, lam));
+    } else {
+        CK(h, h->ops->lam_import(h, in, lam));
+    }
+    return QLBM_OK;
+}
+
+int export_lam(qlbm_ctx *h, const void *lam, double *out, int ptr_kind)
+{
+    const size_t bytes = (size_t)h->b * 4 * (size_t)h->g.N * sizeof(double);
+    if (ptr_kind == QLBM_HOST) {
+        int rc = ensure_staging(h, bytes);
+        if (rc) return rc;
+        CK(h, h->ops->lam_export(h, lam, h->staging));
+        CK(h, cudaMemcpyAsync(out, h->staging, bytes, cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        CK(h, h->ops->lam_export(h, lam, out));
+    }
+    return QLBM_OK;
+}
+
 }  // namespace
 
 namespace qlbm {
@@ -171,6 +248,11 @@ void qlbm_destroy(qlbm_handle h)
     if (h->partials) cudaFree(h->partials);
     if (h->red_out) cudaFree(h->red_out);
     if (h->staging) cudaFree(h->staging);
+    for (int i = 0; i < 2; ++i)
+        if (h->lam[i]) cudaFree(h->lam[i]);
+    if (h->dtau_acc) cudaFree(h->dtau_acc);
+    if (h->scratch_state) cudaFree(h->scratch_state);
+    free_rollout(h);
     delete h;
 }
 
@@ -208,6 +290,7 @@ int qlbm_init_equilibrium(qlbm_handle h, const double *rho4, const double *u, co
     }
     h->parity = 0;
     h->t = 0;
+    h->ro_steps = -1;
     return QLBM_OK;
 }
 
@@ -220,6 +303,7 @@ int qlbm_step(qlbm_handle h, int64_t nsteps)
         h->parity ^= 1;
         h->t += 1;
     }
+    if (nsteps > 0) h->ro_steps = -1;   // the recorded rollout no longer ends at the current state
     return QLBM_OK;
 }
 
@@ -298,6 +382,131 @@ int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind)
     }
     h->parity = 0;
     h->t = 0;
+    h->ro_steps = -1;
+    return QLBM_OK;
+}
+
+int qlbm_step_adjoint(qlbm_handle h, const double *lam_next, double *lam, double *dJ_dtau, int ptr_kind)
+{
+    if (!valid(h) || !lam_next || !lam) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_step_adjoint: bad argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    int rc = ensure_reverse(h);
+    if (rc) return rc;
+    const void *state = h->pop;
+    if (h->parity) {
+        if (!h->scratch_state) CK(h, cudaMalloc(&h->scratch_state, h->state_bytes()));
+        CK(h, h->ops->copy_natural(h, h->scratch_state));
+        state = h->scratch_state;
+    }
+    if ((rc = import_lam(h, lam_next, ptr_kind, h->lam[0]))) return rc;
+    CK(h, cudaMemsetAsync(h->dtau_acc, 0, (size_t)site_blocks(h) * sizeof(double), h->stream));
+    CK(h, h->ops->adjoint(h, state, h->lam[0], h->lam[1]));
+    if ((rc = export_lam(h, h->lam[1], lam, ptr_kind))) return rc;
+    double g = 0.0;
+    if ((rc = read_dtau(h, &g))) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (dJ_dtau) *dJ_dtau = g;
+    return check_flags(h);
+}
+
+int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval)
+{
+    if (!valid(h) || nsteps < 0 || interval < 0) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_rollout: bad argument");
+    int64_t K = interval;
+    if (K == 0) {
+        K = 1;
+        while (K * K < nsteps) ++K;
+    }
+    const int64_t nseg = (nsteps + K - 1) / K;
+    const int64_t need_seg = K > 1 ? K - 1 : 0;
+    if (h->ck_slots < nseg || h->seg_slots < need_seg) {
+        free_rollout(h);
+        const size_t sb = h->state_bytes();
+        if (nseg > 0) {
+            cudaError_t e = cudaMalloc(&h->ck, sb * (size_t)nseg);
+            if (e == cudaSuccess && need_seg > 0) e = cudaMalloc(&h->seg, sb * (size_t)need_seg);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                free_rollout(h);
+                char buf[256];
+                snprintf(buf, sizeof(buf), "qlbm_rollout: %lld checkpoints + %lld segment states of %zu bytes "
+                         "do not fit (%s)", (long long)nseg, (long long)need_seg, sb, cudaGetErrorString(e));
+                return fail(h, QLBM_ERR_OOM, buf);
+            }
+        }
+        h->ck_slots = nseg;
+        h->seg_slots = need_seg;
+    }
+    const size_t sb = h->state_bytes();
+    for (int64_t i = 0; i < nsteps; ++i) {
+        if (i % K == 0) CK(h, h->ops->copy_natural(h, static_cast<char *>(h->ck) + sb * (size_t)(i / K)));
+        CK(h, h->ops->step(h, h->parity == 1));
+        h->parity ^= 1;
+        h->t += 1;
+    }
+    h->ro_steps = nsteps;
+    h->ro_interval = K;
+    return QLBM_OK;
+}
+
+int qlbm_rollout_adjoint(qlbm_handle h, const double *lam_T, double *lam_0, double *dJ_dtau, int ptr_kind)
+{
+    if (!valid(h) || !lam_T || !lam_0) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_rollout_adjoint: bad argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    if (h->ro_steps < 0) return fail(h, QLBM_ERR_STATE, "qlbm_rollout_adjoint: no rollout recorded");
+    int rc = ensure_reverse(h);
+    if (rc) return rc;
+    if ((rc = import_lam(h, lam_T, ptr_kind, h->lam[0]))) return rc;
+    CK(h, cudaMemsetAsync(h->dtau_acc, 0, (size_t)site_blocks(h) * sizeof(double), h->stream));
+    const int64_t N = h->ro_steps, K = h->ro_interval;
+    const size_t sb = h->state_bytes();
+    int cur = 0;
+    for (int64_t seg = (N + K - 1) / K - 1; seg >= 0; --seg) {
+        const int64_t len = (N - seg * K) < K ? (N - seg * K) : K;
+        auto slot = [&](int64_t j) -> void * {
+            return j == 0 ? static_cast<char *>(h->ck) + sb * (size_t)seg
+                          : static_cast<char *>(h->seg) + sb * (size_t)(j - 1);
+        };
+        for (int64_t j = 1; j < len; ++j) CK(h, h->ops->push(h, slot(j - 1), slot(j)));
+        for (int64_t j = len - 1; j >= 0; --j) {
+            CK(h, h->ops->adjoint(h, slot(j), h->lam[cur], h->lam[1 - cur]));
+            cur ^= 1;
+        }
+    }
+    if ((rc = export_lam(h, h->lam[cur], lam_0, ptr_kind))) return rc;
+    double g = 0.0;
+    if ((rc = read_dtau(h, &g))) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (dJ_dtau) *dJ_dtau = g;
+    return check_flags(h);
+}
+
+int qlbm_init_equilibrium_adjoint(qlbm_handle h, const double *rho4, const double *u, const double *eps,
+                                  const double *lam0, double *g_rho4, double *g_u, double *g_eps, int ptr_kind)
+{
+    if (!valid(h) || !rho4 || !u || !lam0)
+        return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_init_equilibrium_adjoint: null argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    if (ptr_kind == QLBM_DEVICE) {
+        CK(h, h->ops->init_adjoint(h, lam0, rho4, u, eps, g_rho4, g_u, g_eps));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return QLBM_OK;
+    }
+    const size_t N = (size_t)h->g.N, fd = field_doubles(h), ld = (size_t)h->b * 4 * N;
+    int rc = ensure_staging(h, (2 * fd + ld) * sizeof(double));
+    if (rc) return rc;
+    double *r = h->staging, *uu = r + 4 * N, *ee = uu + (size_t)h->d * N;
+    double *gr = h->staging + fd, *gu = gr + 4 * N, *ge = gu + (size_t)h->d * N;
+    double *l = h->staging + 2 * fd;
+    CK(h, cudaMemcpyAsync(r, rho4, 4 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(uu, u, (size_t)h->d * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (eps) CK(h, cudaMemcpyAsync(ee, eps, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(l, lam0, ld * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, h->ops->init_adjoint(h, l, r, uu, eps ? ee : nullptr, gr, gu, ge));
+    if (g_rho4) CK(h, cudaMemcpyAsync(g_rho4, gr, 4 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (g_u) CK(h, cudaMemcpyAsync(g_u, gu, (size_t)h->d * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (g_eps) CK(h, cudaMemcpyAsync(g_eps, ge, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
     return QLBM_OK;
 }
 

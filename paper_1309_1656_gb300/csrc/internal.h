@@ -49,6 +49,16 @@ struct qlbm_ctx {
     size_t staging_bytes = 0;
     const qlbm::LatticeOps *ops = nullptr;
     std::string err;
+    // reverse mode
+    void *lam[2] = {nullptr, nullptr};  // cotangent planes (arithmetic type), natural order
+    double *dtau_acc = nullptr;         // per-block dJ/dtau accumulators
+    void *scratch_state = nullptr;      // one natural-order state (single adjoint step)
+    void *ck = nullptr;                 // rollout checkpoints
+    void *seg = nullptr;                // rollout segment states (interval - 1 of them)
+    int64_t ck_slots = 0, seg_slots = 0;
+    int64_t ro_steps = -1, ro_interval = 0;   // last rollout (-1: none)
+    size_t state_bytes() const { return (size_t)b * 4 * (size_t)g.P * elem_bytes; }
+    size_t lam_bytes() const { return (size_t)b * 4 * (size_t)g.P * (prec == QLBM_FP64 ? 8 : 4); }
 };
 
 namespace qlbm {
@@ -60,6 +70,14 @@ struct LatticeOps {
     cudaError_t (*set_state)(qlbm_ctx *h, const double *in);
     cudaError_t (*moments)(qlbm_ctx *h, double *rho4, double *u, double *eps);
     cudaError_t (*conserved_partial)(qlbm_ctx *h);
+    // reverse mode (state buffers are natural-order copies with the layout of pop)
+    cudaError_t (*adjoint)(qlbm_ctx *h, const void *state, const void *lam_in, void *lam_out);
+    cudaError_t (*push)(qlbm_ctx *h, const void *src, void *dst);
+    cudaError_t (*copy_natural)(qlbm_ctx *h, void *dst);
+    cudaError_t (*lam_import)(qlbm_ctx *h, const double *in, void *lam);
+    cudaError_t (*lam_export)(qlbm_ctx *h, const void *lam, double *out);
+    cudaError_t (*init_adjoint)(qlbm_ctx *h, const double *lam, const double *rho4, const double *u,
+                                const double *eps, double *grho4, double *gu, double *geps);
 };
 
 const LatticeOps *lattice_ops_d2q9(int prec);

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "internal.h"
+#include "adjoint.cuh"
 #include "kernels.cuh"
 
 namespace qlbm {
@@ -76,13 +77,14 @@ template <int D, class Codec> struct Launchers {
     using R = typename Codec::R;
     static constexpr int Q = Lattice<D>::Q;
 
-    static Planes<S, Q> planes(const qlbm_ctx *h)
+    template <class T> static Planes<T, Q> planes_of(const qlbm_ctx *h, const void *base)
     {
-        Planes<S, Q> pl;
-        S *base = static_cast<S *>(h->pop);
-        for (int k = 0; k < 4 * Q; ++k) pl.p[k] = base + (int64_t)k * h->g.P;
+        Planes<T, Q> pl;
+        T *b = static_cast<T *>(const_cast<void *>(base));
+        for (int k = 0; k < 4 * Q; ++k) pl.p[k] = b + (int64_t)k * h->g.P;
         return pl;
     }
+    static Planes<S, Q> planes(const qlbm_ctx *h) { return planes_of<S>(h, h->pop); }
 
     static cudaError_t step(qlbm_ctx *h, bool odd)
     {
@@ -148,10 +150,62 @@ template <int D, class Codec> struct Launchers {
         return cudaGetLastError();
     }
 
+    static cudaError_t adjoint(qlbm_ctx *h, const void *state, const void *lam_in, void *lam_out)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        k_adjoint<D, Codec><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, state), planes_of<R>(h, lam_in),
+                                                        planes_of<R>(h, lam_out), h->g, make_coll<R>(h),
+                                                        make_codec<Codec>(h), h->dtau_acc);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t push(qlbm_ctx *h, const void *src, void *dst)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        k_step_push<D, Codec><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, src), planes_of<S>(h, dst), h->g,
+                                                          make_coll<R>(h), make_codec<Codec>(h), h->flags);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t copy_natural(qlbm_ctx *h, void *dst)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        if (h->parity)
+            k_copy_natural<D, Codec, true><<<grd, blk, 0, h->stream>>>(planes(h), planes_of<S>(h, dst), h->g,
+                                                                       make_codec<Codec>(h));
+        else
+            k_copy_natural<D, Codec, false><<<grd, blk, 0, h->stream>>>(planes(h), planes_of<S>(h, dst), h->g,
+                                                                        make_codec<Codec>(h));
+        return cudaGetLastError();
+    }
+
+    static cudaError_t lam_import(qlbm_ctx *h, const double *in, void *lam)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        k_lam_import<D, R><<<grd, blk, 0, h->stream>>>(in, planes_of<R>(h, lam), h->g);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t lam_export(qlbm_ctx *h, const void *lam, double *out)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        k_lam_export<D, R><<<grd, blk, 0, h->stream>>>(planes_of<R>(h, lam), h->g, out);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t init_adjoint(qlbm_ctx *h, const double *lam, const double *rho4, const double *u,
+                                    const double *eps, double *grho4, double *gu, double *geps)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        k_init_adjoint<D><<<grd, blk, 0, h->stream>>>(lam, h->g, make_init(h), rho4, u, eps, grho4, gu, geps);
+        return cudaGetLastError();
+    }
+
     static const LatticeOps *table()
     {
-        static const LatticeOps t = {&step, &init_eq, &get_state, &set_state, &moments,
-                                     &conserved_partial};
+        static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
+                                     &conserved_partial, &adjoint, &push, &copy_natural, &lam_import,
+                                     &lam_export, &init_adjoint};
         return &t;
     }
 };

@@ -65,6 +65,10 @@ _moments = _sig("qlbm_moments", _i, [_vp, _vp, _vp, _vp, _i])
 _conserved = _sig("qlbm_conserved", _i, [_vp, _vp])
 _get_state = _sig("qlbm_get_state", _i, [_vp, _vp, _i])
 _set_state = _sig("qlbm_set_state", _i, [_vp, _vp, _i])
+_step_adjoint = _sig("qlbm_step_adjoint", _i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i])
+_rollout = _sig("qlbm_rollout", _i, [_vp, _i64, _i64])
+_rollout_adjoint = _sig("qlbm_rollout_adjoint", _i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i])
+_init_adjoint = _sig("qlbm_init_equilibrium_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i])
 _conserved_static = _sig("qlbm_conserved_static", _i, [_i, ctypes.POINTER(_i64), _d, _vp, _vp, _vp])
 
 
@@ -172,6 +176,31 @@ def qlbm_set_state(h, buf):
     _check(_set_state(h, p, k), h)
 
 
+def qlbm_step_adjoint(h, lam_next, lam):
+    """One reverse step at the current state; fills lam, returns dJ/dtau part."""
+    p = [_ptr(lam_next), _ptr(lam)]
+    g = _d(0.0)
+    _check(_step_adjoint(h, p[0][0], p[1][0], ctypes.byref(g), _kind(*p)), h)
+    return g.value
+
+
+def qlbm_rollout(h, nsteps, interval=0):
+    _check(_rollout(h, int(nsteps), int(interval)), h)
+
+
+def qlbm_rollout_adjoint(h, lam_T, lam_0):
+    """Reverse sweep over the last rollout; fills lam_0, returns dJ/dtau."""
+    p = [_ptr(lam_T), _ptr(lam_0)]
+    g = _d(0.0)
+    _check(_rollout_adjoint(h, p[0][0], p[1][0], ctypes.byref(g), _kind(*p)), h)
+    return g.value
+
+
+def qlbm_init_equilibrium_adjoint(h, rho4, u, eps, lam0, g_rho4=None, g_u=None, g_eps=None):
+    p = [_ptr(rho4), _ptr(u), _ptr(eps), _ptr(lam0), _ptr(g_rho4), _ptr(g_u), _ptr(g_eps)]
+    _check(_init_adjoint(h, *[x[0] for x in p], _kind(*p)), h)
+
+
 def qlbm_conserved_static(lattice, dims, beta0, state, out, stream=None):
     """The eight global averages of qlbm_conserved for a caller-owned device
     state (canonical layout [b][4][N], float64) into a caller-owned device
@@ -203,6 +232,7 @@ class Lattice:
         self.b = 9 if self.d == 2 else 19
         self.dims = tuple(int(v) for v in (list(dims) + [1] * (3 - len(dims))))
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        self.tau, self.beta0, self.dt = float(tau), float(beta0), float(dt)
         self.h = qlbm_create(lattice, self.dims, tau, beta0, dt, precision, stream)
 
     def close(self):
@@ -254,3 +284,16 @@ class Lattice:
 
     def set_state(self, state):
         qlbm_set_state(self.h, np.ascontiguousarray(state, dtype=np.float64))
+
+    def step_adjoint(self, lam_next):
+        lam = np.zeros((self.b, 4, self.N))
+        g = qlbm_step_adjoint(self.h, np.ascontiguousarray(lam_next, dtype=np.float64), lam)
+        return lam, g
+
+    def rollout(self, nsteps, interval=0):
+        qlbm_rollout(self.h, nsteps, interval)
+
+    def rollout_adjoint(self, lam_T):
+        lam = np.zeros((self.b, 4, self.N))
+        g = qlbm_rollout_adjoint(self.h, np.ascontiguousarray(lam_T, dtype=np.float64), lam)
+        return lam, g
