@@ -15,6 +15,8 @@ ends with the FP64 conservation reduction.  Reported:
   fp64        the same for FP64 storage
   e2e         MLUPS through the C ABI with host buffers: init from pinned
               host fields, K steps, moments back to pinned host memory
+  adjoint     reverse sweep time (segment recomputation + adjoint steps) /
+              plain forward time over the same 256 steps, FP32
   cpu_baseline  the FP64 oracle on a 32^3 sample on the host cores
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -233,6 +235,55 @@ def bench_ours(args):
         del lat
         torch.cuda.synchronize()
 
+    # reverse mode: checkpointed rollout + adjoint sweep vs a plain forward
+    adj = None
+    if "fp32" in results and args.adjoint_steps > 0:
+        NA = args.adjoint_steps
+        lat = qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision="fp32", stream=stream.cuda_stream)
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        lat.step(W)
+        lat.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record(stream)
+        lat.step(NA)
+        ev[1].record(stream)
+        lat.sync()
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        qlbm.qlbm_rollout(lat.h, NA, 0)
+        ev[3].record(stream)
+        # observable: total spin magnetisation s_z in the central (L/4)^d box
+        lam_T = torch.zeros((b, 4, N), dtype=torch.float64, device="cuda")
+        grid = np.zeros(dims[::-1], bool)
+        sl = tuple(slice(n // 2 - max(1, n // 8), n // 2 + max(1, n // 8)) for n in dims[::-1])
+        grid[sl] = True
+        lam_T[:, 3, torch.from_numpy(grid.ravel()).cuda()] = 1.0
+        lam_0 = torch.empty_like(lam_T)
+        torch.cuda.synchronize()
+        ev[4].record(stream)
+        dJdtau = qlbm.qlbm_rollout_adjoint(lat.h, lam_T, lam_0)
+        ev[5].record(stream)
+        torch.cuda.synchronize()
+        t_plain = ev[0].elapsed_time(ev[1])
+        t_roll = ev[2].elapsed_time(ev[3])
+        t_adj = ev[4].elapsed_time(ev[5])
+        t_plain = max_over_ranks(t_plain)
+        t_roll = max_over_ranks(t_roll)
+        t_adj = max_over_ranks(t_adj)
+        interval = 1
+        while interval * interval < NA:
+            interval += 1
+        adj = {"ratio": round(t_adj / t_plain, 3), "unit": "adjoint sweep time / forward time",
+               "forward_ms": round(t_plain, 3), "rollout_ms": round(t_roll, 3),
+               "adjoint_ms": round(t_adj, 3), "rollout_overhead": round(t_roll / t_plain, 3),
+               "steps": NA, "interval": interval, "precision": "fp32",
+               "observable": "sum of s_z over the central box", "dJ_dtau": dJdtau,
+               "note": "adjoint sweep = segment recomputation (two-buffer forward) + reverse steps"}
+        lat.close()
+        del lat, lam_T, lam_0
+        torch.cuda.synchronize()
+
     # end-to-end through the C ABI with pinned host buffers
     e2e = None
     if "fp32" in results and not args.no_e2e:
@@ -301,6 +352,8 @@ def bench_ours(args):
         line["clocks"] = clocks
     if e2e:
         line["e2e"] = e2e
+    if adj:
+        line["adjoint"] = adj
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -381,6 +434,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

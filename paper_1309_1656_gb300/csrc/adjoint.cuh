@@ -96,11 +96,114 @@ __device__ __forceinline__ double block_sum_double(double v)
     return acc;
 }
 
+// Weighted moments of a cotangent component over the directions:
+// sum_i w_i v_i (1, i, |i|^2, i i^T), accumulated one direction at a time.
+template <typename R> struct MuMom {
+    R m0, mx, my, mz, m2, xx, yy, zz, xy, xz, yz;
+    __device__ __forceinline__ void zero() { m0 = mx = my = mz = m2 = xx = yy = zz = xy = xz = yz = R(0); }
+    template <int D, int q> __device__ __forceinline__ void add(R a)
+    {
+        constexpr int X = cx<D>(q), Y = cy<D>(q), Z = cz<D>(q);
+        m0 += a;
+        if (X) mx += X * a;
+        if (Y) my += Y * a;
+        if (Z) mz += Z * a;
+        if (X * X + Y * Y + Z * Z) m2 += (X * X + Y * Y + Z * Z) * a;
+        if (X) xx += a;
+        if (Y) yy += a;
+        if (Z) zz += a;
+        if (X * Y) xy += (X * Y) * a;
+        if (X * Z) xz += (X * Z) * a;
+        if (Y * Z) yz += (Y * Z) * a;
+    }
+    // sum_i w_i v_i P_i with P_i = 1 + a2 (K|i|^2 - c) + c3 i.j + c4 (i.j)^2 + c5 |j|^2
+    __device__ __forceinline__ R wP(R a2, R K, R c, R c3, R c4, R c5, R jx, R jy, R jz, R jj) const
+    {
+        const R quad = jx * (xx * jx + xy * jy + xz * jz) + jy * (xy * jx + yy * jy + yz * jz) +
+                       jz * (xz * jx + yz * jy + zz * jz);
+        return m0 * (R(1) + c5 * jj) + a2 * (K * m2 - c * m0) + c3 * (mx * jx + my * jy + mz * jz) + c4 * quad;
+    }
+    // (sum_i w_i v_i i i^T) j
+    __device__ __forceinline__ void Mj(R jx, R jy, R jz, R &ox, R &oy, R &oz) const
+    {
+        ox = xx * jx + xy * jy + xz * jz;
+        oy = xy * jx + yy * jy + yz * jz;
+        oz = xz * jx + yz * jy + zz * jz;
+    }
+};
+
+template <int D, class Codec, int q>
+__device__ __forceinline__ void adj_accumulate(const Planes<typename Codec::S, Lattice<D>::Q> &st,
+                                               const Planes<typename Codec::R, Lattice<D>::Q> &lin,
+                                               const Grid &g, const SiteIdx &si, const Codec &codec,
+                                               const Coll<typename Codec::R> &k, typename Codec::R (&fw)[8],
+                                               typename Codec::R &dot, MuMom<typename Codec::R> &A,
+                                               MuMom<typename Codec::R> &Bx, MuMom<typename Codec::R> &By,
+                                               MuMom<typename Codec::R> &Bz)
+{
+    using R = typename Codec::R;
+    const R f = codec.load(st.p[4 * q][si.s]);
+    const R sx = codec.load(st.p[4 * q + 1][si.s]);
+    const R sy = codec.load(st.p[4 * q + 2][si.s]);
+    const R sz = codec.load(st.p[4 * q + 3][si.s]);
+    const int s = neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q));
+    const R mf = lin.p[4 * q][s], mx = lin.p[4 * q + 1][s], my = lin.p[4 * q + 2][s], mz = lin.p[4 * q + 3][s];
+    fw[0] += f;
+    fw[1] += sx;
+    fw[2] += sy;
+    fw[3] += sz;
+    if (cx<D>(q)) fw[4] += cx<D>(q) * f;
+    if (cy<D>(q)) fw[5] += cy<D>(q) * f;
+    if (cz<D>(q)) fw[6] += cz<D>(q) * f;
+    if (cnorm2<D>(q)) fw[7] += cnorm2<D>(q) * f;
+    dot += mf * f + mx * sx + my * sy + mz * sz;
+    const R w = k.w[cnorm2<D>(q)];
+    A.template add<D, q>(w * mf);
+    Bx.template add<D, q>(w * mx);
+    By.template add<D, q>(w * my);
+    Bz.template add<D, q>(w * mz);
+}
+
+template <int D, class Codec, int q>
+struct AdjLoop {
+    static __device__ __forceinline__ void run(const Planes<typename Codec::S, Lattice<D>::Q> &st,
+                                               const Planes<typename Codec::R, Lattice<D>::Q> &lin,
+                                               const Grid &g, const SiteIdx &si, const Codec &codec,
+                                               const Coll<typename Codec::R> &k, typename Codec::R (&fw)[8],
+                                               typename Codec::R &dot, MuMom<typename Codec::R> &A,
+                                               MuMom<typename Codec::R> &Bx, MuMom<typename Codec::R> &By,
+                                               MuMom<typename Codec::R> &Bz)
+    {
+        adj_accumulate<D, Codec, q>(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
+        AdjLoop<D, Codec, q + 1>::run(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
+    }
+};
+template <int D, class Codec> struct AdjLoop<D, Codec, Lattice<D>::Q> {
+    static __device__ __forceinline__ void run(const Planes<typename Codec::S, Lattice<D>::Q> &,
+                                               const Planes<typename Codec::R, Lattice<D>::Q> &,
+                                               const Grid &, const SiteIdx &, const Codec &,
+                                               const Coll<typename Codec::R> &, typename Codec::R (&)[8],
+                                               typename Codec::R &, MuMom<typename Codec::R> &,
+                                               MuMom<typename Codec::R> &, MuMom<typename Codec::R> &,
+                                               MuMom<typename Codec::R> &)
+    {
+    }
+};
+
 // One reverse step.  state: W^n in natural order; lam_in: lambda^{n+1};
 // lam_out: lambda^n (natural order, arithmetic type R).  dtau_acc[block] +=
 // this block's sum_k mu_k.(W^eq_k - W_k) (times d omega/d tau on the host).
+//
+// Pass 1 reads W^n and mu together and folds them straight into
+// accumulators: the forward moments, sum_k mu_k.W_k, and the weighted
+// cotangent moments sum_k w_k mu_k (1, i_k, |i_k|^2, i_k i_k^T).  Every
+// per-direction sum of the transpose above is a polynomial of degree <= 2 in
+// i_k times w_k mu_k, so these moments give them once the forward moments
+// are known.  Pass 2 re-reads mu (cache hits; the index carries the
+// run-time zero so the compiler does not keep pass 1's values live) and
+// writes lambda^n.
 template <int D, class Codec>
-__global__ void __launch_bounds__(kAdjBlock)
+__global__ void __launch_bounds__(kAdjBlock, Codec::MIN_BLOCKS)
 k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typename Codec::R, Lattice<D>::Q> lin,
           const Planes<typename Codec::R, Lattice<D>::Q> lout, Grid g, Coll<typename Codec::R> k,
           Codec codec, double *__restrict__ dtau_acc)
@@ -112,64 +215,81 @@ k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typena
     const bool active = site_of_block(g, si);
     double dtau = 0.0;
     if (active) {
-        R f[Q], sx[Q], sy[Q], sz[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            f[q] = codec.load(st.p[4 * q][si.s]);
-            sx[q] = codec.load(st.p[4 * q + 1][si.s]);
-            sy[q] = codec.load(st.p[4 * q + 2][si.s]);
-            sz[q] = codec.load(st.p[4 * q + 3][si.s]);
-        }
-        const FwdSite<D, R, DEV> m = forward_moments<D, R, DEV>(f, sx, sy, sz, k);
-        R Af = R(0), Asx = R(0), Asy = R(0), Asz = R(0), sP = R(0), G = R(0);
-        R Jbx = R(0), Jby = R(0), Jbz = R(0);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int s = neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q));
-            const R mf = lin.p[4 * q][s], mx = lin.p[4 * q + 1][s], my = lin.p[4 * q + 2][s],
-                    mz = lin.p[4 * q + 3][s];
-            const R w = k.w[cnorm2<D>(q)];
-            const R P1 = P1_of<D, R, DEV>(m, k, q);
-            const R wP = w * (R(1) + P1);
-            Af += wP * mf;
-            Asx += wP * mx;
-            Asy += wP * my;
-            Asz += wP * mz;
-            const R Pbar = k.omega * w * (m.n * mf + m.Sx * mx + m.Sy * my + m.Sz * mz);
-            sP += Pbar;
-            G += Pbar * (k.K * cnorm2<D>(q) - k.c);
-            const R t = cx<D>(q) * m.jx + cy<D>(q) * m.jy + cz<D>(q) * m.jz;
-            const R T = Pbar * (k.c3 + R(2) * k.c4 * t);
-            Jbx += cx<D>(q) * T;
-            Jby += cy<D>(q) * T;
-            Jbz += cz<D>(q) * T;
-            // W^eq - W: f-part (deviation form: w ((P-1) n + dn) - d)
-            const R feq_minus = DEV ? w * (P1 * m.n + m.dn) - f[q] : wP * m.n - f[q];
-            dtau += (double)(mf * feq_minus + mx * (wP * m.Sx - sx[q]) + my * (wP * m.Sy - sy[q]) +
-                             mz * (wP * m.Sz - sz[q]));
-        }
-        const R rn = R(1) / m.n;
+        R fw[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // sum f, S, J, E2
+        R dot = R(0);
+        MuMom<R> A, Bx, By, Bz;
+        A.zero();
+        Bx.zero();
+        By.zero();
+        Bz.zero();
+        AdjLoop<D, Codec, 0>::run(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
+        // forward moments
+        const R dn = DEV ? fw[0] : fw[0] - R(1);
+        const R n = DEV ? R(1) + fw[0] : fw[0];
+        const R rn = R(1) / n;
+        const R Sx = fw[1], Sy = fw[2], Sz = fw[3];
+        const R jx = fw[4] * rn, jy = fw[5] * rn, jz = fw[6] * rn;
+        const R jj = jx * jx + jy * jy + jz * jz;
+        const R de = DEV ? (fw[7] - k.S2 * fw[0]) * rn : fw[7] * rn - k.S2;   // E2/n - S2
+        const R e2n = k.S2 + de;
+        const R a2 = k.K * (de - jj) * k.inv_mc2;
+        // sum_k w_k P_k mu_k
+        const R Af = A.wP(a2, k.K, k.c, k.c3, k.c4, k.c5, jx, jy, jz, jj);
+        const R Asx = Bx.wP(a2, k.K, k.c, k.c3, k.c4, k.c5, jx, jy, jz, jj);
+        const R Asy = By.wP(a2, k.K, k.c, k.c3, k.c4, k.c5, jx, jy, jz, jj);
+        const R Asz = Bz.wP(a2, k.K, k.c, k.c3, k.c4, k.c5, jx, jy, jz, jj);
+        // Pbar_k / omega = n w_k mu_f,k + S.w_k mu_s,k  ->  its moments
+        const R p0 = n * A.m0 + Sx * Bx.m0 + Sy * By.m0 + Sz * Bz.m0;
+        const R p2 = n * A.m2 + Sx * Bx.m2 + Sy * By.m2 + Sz * Bz.m2;
+        const R p1x = n * A.mx + Sx * Bx.mx + Sy * By.mx + Sz * Bz.mx;
+        const R p1y = n * A.my + Sx * Bx.my + Sy * By.my + Sz * Bz.my;
+        const R p1z = n * A.mz + Sx * Bx.mz + Sy * By.mz + Sz * Bz.mz;
+        R qx, qy, qz, tx, ty, tz;
+        A.Mj(jx, jy, jz, qx, qy, qz);
+        qx *= n;
+        qy *= n;
+        qz *= n;
+        Bx.Mj(jx, jy, jz, tx, ty, tz);
+        qx += Sx * tx;
+        qy += Sx * ty;
+        qz += Sx * tz;
+        By.Mj(jx, jy, jz, tx, ty, tz);
+        qx += Sy * tx;
+        qy += Sy * ty;
+        qz += Sy * tz;
+        Bz.Mj(jx, jy, jz, tx, ty, tz);
+        qx += Sz * tx;
+        qy += Sz * ty;
+        qz += Sz * tz;
+        const R sP = k.omega * p0;
+        const R G = k.omega * (k.K * p2 - k.c * p0);
         const R cj = R(2) * (k.c5 * sP - k.K * k.inv_mc2 * G);
-        const R jbx = Jbx + cj * m.jx, jby = Jby + cj * m.jy, jbz = Jbz + cj * m.jz;
+        const R jbx = k.omega * (k.c3 * p1x + R(2) * k.c4 * qx) + cj * jx;
+        const R jby = k.omega * (k.c3 * p1y + R(2) * k.c4 * qy) + cj * jy;
+        const R jbz = k.omega * (k.c3 * p1z + R(2) * k.c4 * qz) + cj * jz;
         const R ebar = k.K * k.inv_mc2 * G;
-        const R nbar = k.omega * Af - (jbx * m.jx + jby * m.jy + jbz * m.jz + ebar * m.e2n) * rn;
-        const R Jx = jbx * rn, Jy = jby * rn, Jz = jbz * rn, Eb = ebar * rn;
+        const R nbar = k.omega * Af - (jbx * jx + jby * jy + jbz * jz + ebar * e2n) * rn;
+        const R Jbx2 = jbx * rn, Jby2 = jby * rn, Jbz2 = jbz * rn, Eb = ebar * rn;
         const R omc = R(1) - k.omega;
-        // second pass: mu reloaded (offset by the run-time zero so the first
-        // pass's 4b values are not kept live in registers)
-        SiteIdx so = si;
-        so.s += g.zero;
-        so.x += g.zero;
+        const R Sbx = k.omega * Asx, Sby = k.omega * Asy, Sbz = k.omega * Asz;
+        // sum_k mu_k.(W^eq_k - W_k): f-part n Af - sum mu_f f (deviation form
+        // subtracts sum w mu_f = A.m0 as well), spin part S.As - sum mu_s.s
+        const R eqdot = (DEV ? (Af - A.m0) + dn * Af : n * Af) + Sx * Asx + Sy * Asy + Sz * Asz;
+        dtau = (double)(eqdot - dot);
+        // pass 2: lambda^n
+        SiteIdx s2 = si;
+        s2.s += g.zero;
+        s2.x += g.zero;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int s = neighbour(g, so, cx<D>(q), cy<D>(q), cz<D>(q));
+            const int s = neighbour(g, s2, cx<D>(q), cy<D>(q), cz<D>(q));
             const R mf = lin.p[4 * q][s], mx = lin.p[4 * q + 1][s], my = lin.p[4 * q + 2][s],
                     mz = lin.p[4 * q + 3][s];
-            lout.p[4 * q][so.s] = omc * mf + nbar + (cx<D>(q) * Jx + cy<D>(q) * Jy + cz<D>(q) * Jz) +
-                                  cnorm2<D>(q) * Eb;
-            lout.p[4 * q + 1][so.s] = omc * mx + k.omega * Asx;
-            lout.p[4 * q + 2][so.s] = omc * my + k.omega * Asy;
-            lout.p[4 * q + 3][so.s] = omc * mz + k.omega * Asz;
+            lout.p[4 * q][s2.s] = omc * mf + nbar +
+                                  (cx<D>(q) * Jbx2 + cy<D>(q) * Jby2 + cz<D>(q) * Jbz2) + cnorm2<D>(q) * Eb;
+            lout.p[4 * q + 1][s2.s] = omc * mx + Sbx;
+            lout.p[4 * q + 2][s2.s] = omc * my + Sby;
+            lout.p[4 * q + 3][s2.s] = omc * mz + Sbz;
         }
     }
     const double bs = block_sum_double<R>(dtau);
