@@ -25,7 +25,6 @@ no exchange step in this build); value = all ranks' site updates / max time.
 """
 import argparse
 import hashlib
-import glob
 import json
 import os
 import statistics
@@ -65,10 +64,15 @@ def make_fields(w):
     raise ValueError(w["kind"])
 
 
-def kernel_source_hash():
+STEP_KERNEL_SOURCES = ("lattice.cuh", "kernels.cuh")
+
+
+def kernel_source_hash(files=STEP_KERNEL_SOURCES):
+    """Hash of the sources that define the step kernel (collision + AA
+    addressing); a recorded DRAM traffic is used only while it matches."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1309_1656_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
+    for name in files:
+        with open(os.path.join(ROOT, "paper_1309_1656_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
