@@ -44,6 +44,9 @@ WORKLOADS = {
     "d3q19-128": dict(d=3, dims=(128, 128, 128), tau=0.7, beta0=1.0, kind="modes", seed=2,
                       desc="D3Q19 128^3 periodic, tau=0.7, beta0=1, Fourier-mode density/velocity/spin "
                            "fields |k|<=4 (RMS 0.02, |u|<=0.05), equilibrium init, eps=eps0"),
+    "d2q9-64": dict(d=2, dims=(64, 64, 1), tau=0.8, beta0=1.0, kind="blob", seed=1,
+                    desc="D2Q9 64^2 periodic, tau=0.8, beta0=1, density 1+0.05 sin(2 pi x/64), Gaussian "
+                         "spin blob sigma=8 (|r|=0.1 n, seeded Bloch axis), u=0, eps=eps0"),
     "d3q19-512": dict(d=3, dims=(512, 512, 512), tau=0.6, beta0=1.0, kind="modes", seed=5,
                       desc="D3Q19 512^3 periodic, tau=0.6, beta0=1, Fourier-mode fields amplitude 0.02"),
     "d2q9-4096": dict(d=2, dims=(4096, 4096, 1), tau=0.7, beta0=1.0, kind="shear", seed=3,
@@ -61,6 +64,8 @@ def make_fields(w):
         return fields.modes(w["d"], w["dims"], seed=w["seed"])
     if w["kind"] == "shear":
         return fields.shear2d(w["dims"][0], w["dims"][1], seed=w["seed"])
+    if w["kind"] == "blob":
+        return fields.blob2d(w["dims"][0], w["dims"][1], seed=w["seed"])
     raise ValueError(w["kind"])
 
 
@@ -313,6 +318,10 @@ def bench_ours(args):
                "h2d_bytes_per_step": (r4.nbytes + uu.nbytes) / K,
                "d2h_bytes_per_step": (out_r.nbytes + out_u.nbytes + out_e.nbytes) / K}
 
+    growth = None
+    if args.error_growth > 0 and rank == 0:
+        growth = error_growth(w, fl, args.error_growth, args.error_every, torch, qlbm)
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -339,19 +348,27 @@ def bench_ours(args):
         "config": {"workload": w["desc"], "lattice": "D3Q19" if d == 3 else "D2Q9",
                    "dims": list(dims), "sites": N, "tau": w["tau"], "beta0": w["beta0"],
                    "precision": prim, "parallelism": "replicas" if ws > 1 else "single-gpu",
-                   "l2": "inputs larger than L2: state %.2f GB > 129 MB, no flush" %
-                         (N * b * 4 * bytes_per_value(prim) / 1e9)},
+                   "l2": ("inputs larger than L2: state %.2f GB > 129 MB, no flush" if
+                          N * b * 4 * bytes_per_value(prim) > 129e6 else
+                          "state %.4f GB fits in the 129 MB L2: L2-resident by construction, "
+                          "not an HBM measurement") % (N * b * 4 * bytes_per_value(prim) / 1e9)},
         "roofline": roof,
         "kernel_mlups": round(r32["kernel_mlups"], 1),
         "conservation_drift_rel": r32["drift"],
         "gpu_launches": K + 2,
     }
-    if "fp64" in results:
-        r = results["fp64"]
-        line["fp64"] = {"value": round(r["mlups"], 1), "unit": "MLUPS",
-                        "kernel_mlups": round(r["kernel_mlups"], 1),
-                        "achieved_gbs": round(r["achieved"], 1), "hbm_frac": round(r["achieved"] / peak, 4),
-                        "conservation_drift_rel": r["drift"]}
+    for p_, r in results.items():
+        if p_ == prim:
+            continue
+        line[p_] = {"value": round(r["mlups"], 1), "unit": "MLUPS",
+                    "kernel_mlups": round(r["kernel_mlups"], 1),
+                    "achieved_gbs": round(r["achieved"], 1), "hbm_frac": round(r["achieved"] / peak, 4),
+                    "conservation_drift_rel": r["drift"]}
+        if p_ == "fp64":
+            # bound by FP64 issue: 2 FP64 lanes/clk/SM x 152 SMs x clock
+            line[p_]["bound"] = "alu (fp64 pipe, see profiles/k_step_aa_d3q19_fp64_128.md)"
+    if growth:
+        line["error_growth"] = growth
     if clocks:
         line["clocks"] = clocks
     if e2e:
@@ -365,9 +382,48 @@ def bench_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def error_growth(w, fl, total, every, torch, qlbm):
+    """Normwise errors of the FP32 and FP16-deviation moment fields against
+    the FP64 run of the same workload, every `every` steps."""
+    d, dims = w["d"], w["dims"]
+    N = dims[0] * dims[1] * dims[2]
+    lats = {p: qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision=p) for p in ("fp64", "fp32", "fp16dev")}
+    for lat in lats.values():
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+    bufs = {p: (torch.empty((4, N), dtype=torch.float64, device="cuda"),
+                torch.empty((d, N), dtype=torch.float64, device="cuda"),
+                torch.empty((N,), dtype=torch.float64, device="cuda")) for p in lats}
+    out = []
+    t = 0
+    while t < total:
+        n = min(every, total - t)
+        for lat in lats.values():
+            lat.step(n)
+        t += n
+        for p, lat in lats.items():
+            qlbm.qlbm_moments(lat.h, *bufs[p])
+        ref = bufs["fp64"]
+
+        def err(a, b_):
+            return float((a - b_).abs().max() / b_.abs().max())
+
+        row = {"step": t}
+        for p in ("fp32", "fp16dev"):
+            r, u, e = bufs[p]
+            row[p] = {"n": err(r[0], ref[0][0]), "S": err(r[1:], ref[0][1:]), "u": err(u, ref[1]),
+                      "eps": err(e, ref[2])}
+        out.append(row)
+    for lat in lats.values():
+        lat.close()
+    return {"reference": "the FP64 GPU run of the same workload (itself within 1e-12/step of the oracle)",
+            "norm": "max |x - x_fp64| / max |x_fp64| per field", "rows": out}
+
+
 def cpu_sample(w, L=32):
     from paper_1309_1656_gb300 import fields
     d = w["d"]
+    if w["kind"] == "blob":
+        return w["dims"], make_fields(w)
     dims = (L, L, L) if d == 3 else (L * 8, L * 8, 1)
     fl = fields.modes(d, dims, seed=w["seed"]) if w["kind"] == "modes" else \
         fields.shear2d(dims[0], dims[1], seed=w["seed"], delta=max(2.0, 80.0 * dims[1] / 4096.0))
@@ -439,6 +495,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=256)
+    ap.add_argument("--error-growth", type=int, default=0,
+                    help="also run FP64/FP32/FP16 side by side for this many steps and report errors")
+    ap.add_argument("--error-every", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

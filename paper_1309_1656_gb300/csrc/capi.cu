@@ -75,6 +75,37 @@ int ensure_reverse(qlbm_ctx *h)
     return QLBM_OK;
 }
 
+// Steps per replay of the captured step graph (an even number, so a replay
+// starts and ends in natural order).
+constexpr int kGraphSteps = 32;
+
+// Captures kGraphSteps alternating even/odd step launches once per handle.
+// Capture goes through a private stream (the legacy default stream cannot
+// be captured); the replay is launched on the handle's stream.
+int ensure_graph(qlbm_ctx *h)
+{
+    if (h->graph) return QLBM_OK;
+    cudaStream_t cs = nullptr;
+    CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = h->stream;
+    h->stream = cs;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (int i = 0; e == cudaSuccess && i < kGraphSteps; ++i) e = h->ops->step(h, (i & 1) == 1);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    h->stream = saved;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->graph = nullptr;
+        h->use_graph = 0;   // fall back to direct launches of the same kernels
+    }
+    return QLBM_OK;
+}
+
 void free_rollout(qlbm_ctx *h)
 {
     if (h->ck) cudaFree(h->ck);
@@ -252,6 +283,7 @@ void qlbm_destroy(qlbm_handle h)
         if (h->lam[i]) cudaFree(h->lam[i]);
     if (h->dtau_acc) cudaFree(h->dtau_acc);
     if (h->scratch_state) cudaFree(h->scratch_state);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
     free_rollout(h);
     delete h;
 }
@@ -297,13 +329,28 @@ int qlbm_init_equilibrium(qlbm_handle h, const double *rho4, const double *u, co
 int qlbm_step(qlbm_handle h, int64_t nsteps)
 {
     if (!valid(h) || nsteps < 0) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_step: bad argument");
+    if (nsteps > 0) h->ro_steps = -1;   // a recorded rollout no longer ends at the current state
+    if (h->use_graph && nsteps >= 2 * kGraphSteps) {
+        if (h->parity == 1) {   // bring the buffer to natural order first
+            CK(h, h->ops->step(h, true));
+            h->parity = 0;
+            h->t += 1;
+            --nsteps;
+        }
+        int rc = ensure_graph(h);
+        if (rc) return rc;
+        while (h->graph && nsteps >= kGraphSteps) {
+            CK(h, cudaGraphLaunch(h->graph, h->stream));
+            h->t += kGraphSteps;
+            nsteps -= kGraphSteps;
+        }
+    }
     for (int64_t i = 0; i < nsteps; ++i) {
         const bool odd = h->parity == 1;
         CK(h, h->ops->step(h, odd));
         h->parity ^= 1;
         h->t += 1;
     }
-    if (nsteps > 0) h->ro_steps = -1;   // the recorded rollout no longer ends at the current state
     return QLBM_OK;
 }
 

@@ -57,6 +57,9 @@ struct qlbm_ctx {
     void *seg = nullptr;                // rollout segment states (interval - 1 of them)
     int64_t ck_slots = 0, seg_slots = 0;
     int64_t ro_steps = -1, ro_interval = 0;   // last rollout (-1: none)
+    // CUDA graph of kGraphSteps consecutive steps starting from natural order
+    cudaGraphExec_t graph = nullptr;
+    int use_graph = 1;
     size_t state_bytes() const { return (size_t)b * 4 * (size_t)g.P * elem_bytes; }
     size_t lam_bytes() const { return (size_t)b * 4 * (size_t)g.P * (prec == QLBM_FP64 ? 8 : 4); }
 };

@@ -187,3 +187,23 @@ def test_device_pointer_paths(q, oracle_mod):
         q.qlbm_set_state(lat.h, st)
         assert lat.time() == 0
         assert np.array_equal(lat.get_state(), host)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_replay_equals_single_launches(q, prec):
+    # qlbm_step(n >= 64) replays a captured 32-step graph; the result must be
+    # bit-identical to n single-step calls, from either AA parity.
+    d, dims = 3, (20, 9, 7)
+    st = fields.random_populations(d, dims, seed=61)
+    for pre in (0, 1):
+        with q.Lattice(d, dims, 0.8, 1.0, precision=prec) as a, \
+                q.Lattice(d, dims, 0.8, 1.0, precision=prec) as b:
+            a.set_state(st)
+            b.set_state(st)
+            a.step(pre)
+            b.step(pre)
+            a.step(101)
+            for _ in range(101):
+                b.step(1)
+            assert a.time() == b.time() == 101 + pre
+            assert np.array_equal(a.get_state(), b.get_state())
