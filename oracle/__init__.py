@@ -94,6 +94,12 @@ def _load():
         lib.oracle_conserved.argtypes = [_i, _pi64, _d, _pd, _pd]
         lib.oracle_adjoint_step.restype = _i
         lib.oracle_adjoint_step.argtypes = [_i, _pi64, _d, _d, _d, _pd, _pd, _pd, _pd, _i]
+        lib.oracle_fd.restype = _d
+        lib.oracle_fd.argtypes = [_d, _d]
+        lib.oracle_fd_moments.restype = _i
+        lib.oracle_fd_moments.argtypes = [_i, _d, _d, _d, _pd]
+        lib.oracle_fd_params.restype = _i
+        lib.oracle_fd_params.argtypes = [_i, _pd, _d, _pd]
         _lib = lib
         return lib
 
@@ -226,3 +232,24 @@ def adjoint_step(d, dims, tau, beta0, state, lam_next, dt=1.0, nthreads=0):
     _check(_load().oracle_adjoint_step(d, cd, tau, beta0, dt, _ptr(st), _ptr(ln), _ptr(lam),
                                        _ptr(g), int(nthreads)), "adjoint_step")
     return lam, float(g[0])
+
+
+def fd(k, x):
+    """Complete Fermi-Dirac integral F_k(x) (Sec. 2.2)."""
+    return _load().oracle_fd(float(k), float(x))
+
+
+def fd_moments(d, beta, mu_up, mu_dn):
+    """(n_up, n_dn, eps) of the FD distribution (Eqs. nFDstdOmega, energyFDstdOmega)."""
+    out = np.zeros(3)
+    _check(_load().oracle_fd_moments(int(d), float(beta), float(mu_up), float(mu_dn), _ptr(out)),
+           "fd_moments")
+    return out
+
+
+def fd_params(d, rho4, eps):
+    """(status, [beta, mu_up, mu_dn, a_x, a_y, a_z]) from rho (Pauli) and eps (Prop. 1)."""
+    r = np.ascontiguousarray(rho4, dtype=np.float64).reshape(4)
+    out = np.zeros(6)
+    rc = _load().oracle_fd_params(int(d), _ptr(r), float(eps), _ptr(out))
+    return rc, out

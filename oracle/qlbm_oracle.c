@@ -660,3 +660,205 @@ int oracle_adjoint_step(int d, const int64_t *dims, double tau, double beta0, do
     *dJ_dtau += total;
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Fermi-Dirac integrals and the parameters of a Fermi-Dirac equilibrium     */
+/* (Sec. 2.2: Prop. 1, Eqs. nFDstdOmega and energyFDstdOmega).               */
+/*                                                                           */
+/* F_k(x) = Gamma(k+1)^-1 int_0^inf t^k / (e^(t-x) + 1) dt, written with      */
+/* t = s^2 as 2/Gamma(k+1) int_0^inf s^(2k+1) / (e^(s^2-x) + 1) ds, whose     */
+/* integrand is smooth for k >= -1/2, and integrated by adaptive composite   */
+/* 20-point Gauss-Legendre quadrature (nodes from Newton's method on the     */
+/* Legendre recurrence), split at the Fermi edge s = sqrt(x).  F_0 and       */
+/* F_-1 use the closed forms the paper states.                               */
+/* ------------------------------------------------------------------------- */
+#define GLN 20
+static double gl_x[GLN], gl_w[GLN];
+static int gl_ready = 0;
+
+static void gl_setup(void)
+{
+    if (gl_ready) return;
+    for (int i = 0; i < GLN; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (GLN + 0.5)), pp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;   /* P_0, P_1 */
+            for (int n = 2; n <= GLN; ++n) {
+                double p2 = ((2.0 * n - 1.0) * z * p1 - (n - 1.0) * p0) / n;
+                p0 = p1;
+                p1 = p2;
+            }
+            pp = GLN * (z * p1 - p0) / (z * z - 1.0);   /* P_n' */
+            double dz = p1 / pp;
+            z -= dz;
+            if (fabs(dz) < 1e-17) break;
+        }
+        gl_x[i] = z;
+        gl_w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+    gl_ready = 1;
+}
+
+static double fermi(double a)   /* 1/(e^a + 1) without overflow */
+{
+    if (a > 0.0) {
+        double e = exp(-a);
+        return e / (1.0 + e);
+    }
+    return 1.0 / (1.0 + exp(a));
+}
+
+static double fd_integrand(double s, double k, double x)
+{
+    return 2.0 * pow(s, 2.0 * k + 1.0) * fermi(s * s - x);
+}
+
+static double gl_panel(double a, double b, double k, double x)
+{
+    double c = 0.5 * (a + b), h = 0.5 * (b - a), acc = 0.0;
+    for (int i = 0; i < GLN; ++i) acc += gl_w[i] * fd_integrand(c + h * gl_x[i], k, x);
+    return acc * h;
+}
+
+/* Bisects a panel until its two halves agree with the whole to within
+   tol_abs (a fixed fraction of the whole integral, so panels where the
+   integrand is negligible stop at once) or to rounding level. */
+static double gl_adaptive(double a, double b, double k, double x, double whole, double tol_abs,
+                          int depth)
+{
+    double m = 0.5 * (a + b);
+    double l = gl_panel(a, m, k, x), r = gl_panel(m, b, k, x);
+    double diff = fabs(l + r - whole);
+    if (depth >= 30 || diff <= tol_abs || diff <= 8e-16 * (fabs(l) + fabs(r))) return l + r;
+    return gl_adaptive(a, m, k, x, l, 0.5 * tol_abs, depth + 1) +
+           gl_adaptive(m, b, k, x, r, 0.5 * tol_abs, depth + 1);
+}
+
+/* Complete Fermi-Dirac integral F_k(x), k = -1, 0 or a value >= -1/2. */
+double oracle_fd(double k, double x)
+{
+    if (k == -1.0) return fermi(-x);                                   /* (1 + e^-x)^-1 */
+    if (k == 0.0) return x > 0.0 ? x + log1p(exp(-x)) : log1p(exp(x)); /* log(1 + e^x) */
+    if (k < -0.5) return NAN;
+    gl_setup();
+    double xe = x > 0.0 ? x : 0.0;
+    double edge = sqrt(xe), top = sqrt(xe + 80.0);
+    double p1 = edge > 0.0 ? gl_panel(0.0, edge, k, x) : 0.0;
+    double p2 = gl_panel(edge, top, k, x);
+    double tol = 1e-15 * (fabs(p1) + fabs(p2));
+    double acc = 0.0;
+    if (edge > 0.0) acc += gl_adaptive(0.0, edge, k, x, p1, tol, 0);
+    acc += gl_adaptive(edge, top, k, x, p2, tol, 0);
+    return acc / tgamma(k + 1.0);
+}
+
+/* Forward map (Eqs. nFDstdOmega, energyFDstdOmega): densities of the two
+   spin species and the internal energy of the Fermi-Dirac distribution with
+   parameters (beta, mu_up, mu_dn).  out = {n_up, n_dn, eps}. */
+int oracle_fd_moments(int d, double beta, double mu_up, double mu_dn, double *out)
+{
+    if ((d != 2 && d != 3) || !(beta > 0.0)) return -1;
+    double h = 0.5 * d, pre = pow(2.0 * M_PI / beta, h);
+    double nu = pre * oracle_fd(h - 1.0, beta * mu_up);
+    double nd = pre * oracle_fd(h - 1.0, beta * mu_dn);
+    double e = h / beta * (oracle_fd(h, beta * mu_up) + oracle_fd(h, beta * mu_dn)) /
+               (oracle_fd(h - 1.0, beta * mu_up) + oracle_fd(h - 1.0, beta * mu_dn));
+    out[0] = nu;
+    out[1] = nd;
+    out[2] = e;
+    return 0;
+}
+
+/* nu solving (2 pi / beta)^h F_{h-1}(nu) = n_s: closed form in 2D
+   (F_0(nu) = log(1 + e^nu)); safeguarded Newton (derivative F_{h-2}) on a
+   bisection bracket in 3D. */
+static double species_nu(int d, double beta, double ns)
+{
+    double h = 0.5 * d, y = ns * pow(beta / (2.0 * M_PI), h);
+    if (d == 2) return y > 30.0 ? y + log(-expm1(-y)) : log(expm1(y));
+    double lo = log(y) - 10.0, hi = (y > 1.0 ? pow(y * tgamma(h + 1.0), 1.0 / h) : log(y)) + 10.0;
+    double nu = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        double F = oracle_fd(h - 1.0, nu) - y;
+        if (F > 0.0) hi = nu;
+        else lo = nu;
+        double step = F / oracle_fd(h - 2.0, nu);
+        double nn = nu - step;
+        if (!(nn > lo && nn < hi)) nn = 0.5 * (lo + hi);
+        if (fabs(nn - nu) <= 1e-15 * (1.0 + fabs(nu)) || hi - lo <= 1e-15 * (1.0 + fabs(nu))) {
+            nu = nn;
+            break;
+        }
+        nu = nn;
+    }
+    return nu;
+}
+
+/* Prop. 1 inverted: the parameters (beta, mu_up, mu_dn) and eigenbasis of the
+   Fermi-Dirac equilibrium whose density matrix rho = (n 1 + S.sigma)/2 and
+   internal energy eps are given.  The eigen-decomposition of rho is taken on
+   the complex 2x2 matrix (characteristic polynomial, eigenvector of the larger
+   eigenvalue), the Bloch axis is that eigenvector's <v|sigma|v>.  beta is
+   found by bisection on log(beta) of
+     g(beta) = (d/2) beta^-1 (2 pi/beta)^(d/2) sum_s F_{d/2}(nu_s(beta)) - n eps,
+   decreasing in beta, bracketed around the classical estimate (d/2)/eps.
+   out = {beta, mu_up, mu_dn, a_x, a_y, a_z}; returns 0, 1 if rho is not
+   positive definite, 2 if no beta fits (eps below the degenerate limit). */
+int oracle_fd_params(int d, const double *rho4, double eps, double *out)
+{
+    if (d != 2 && d != 3) return -1;
+    for (int i = 0; i < 6; ++i) out[i] = NAN;
+    mat2 r;
+    pauli_to_mat(rho4[0], rho4[1], rho4[2], rho4[3], &r);
+    double tr = creal(r.m[0][0] + r.m[1][1]);
+    double det = creal(r.m[0][0] * r.m[1][1] - r.m[0][1] * r.m[1][0]);
+    double disc = sqrt(fmax(0.25 * tr * tr - det, 0.0));
+    double lup = 0.5 * tr + disc, ldn = 0.5 * tr - disc;
+    if (!(ldn > 0.0)) return 1;
+    /* eigenvector of lup: (r01, lup - r00) or (lup - r11, r10), the longer one */
+    cplx v0 = r.m[0][1], v1 = lup - r.m[0][0];
+    cplx w0 = lup - r.m[1][1], w1 = r.m[1][0];
+    if (cabs(w0) * cabs(w0) + cabs(w1) * cabs(w1) > cabs(v0) * cabs(v0) + cabs(v1) * cabs(v1)) {
+        v0 = w0;
+        v1 = w1;
+    }
+    double nv = sqrt(creal(v0 * conj(v0) + v1 * conj(v1)));
+    if (nv > 0.0 && disc > 0.0) {
+        v0 /= nv;
+        v1 /= nv;
+        out[3] = 2.0 * creal(conj(v0) * v1);          /* <v|sigma_x|v> */
+        out[4] = 2.0 * cimag(conj(v0) * v1);          /* <v|sigma_y|v> */
+        out[5] = creal(conj(v0) * v0 - conj(v1) * v1); /* <v|sigma_z|v> */
+    } else {
+        out[3] = out[4] = out[5] = 0.0;               /* degenerate: any axis */
+    }
+    double h = 0.5 * d, nE = tr * eps;
+    if (!(eps > 0.0)) return 2;
+#define G_OF(lb)                                                                            \
+    (h * exp(-(lb)) * pow(2.0 * M_PI * exp(-(lb)), h) *                                      \
+         (oracle_fd(h, species_nu(d, exp(lb), lup)) + oracle_fd(h, species_nu(d, exp(lb), ldn))) - \
+     nE)
+    /* bracket around the classical estimate beta = (d/2)/eps, widened by e */
+    double lb0 = log(h / eps), blo = lb0 - 1.0, bhi = lb0 + 1.0;
+    int tries = 0;
+    while (!(G_OF(blo) > 0.0)) {
+        blo -= 1.0;
+        if (++tries > 30) return 2;
+    }
+    tries = 0;
+    while (!(G_OF(bhi) < 0.0)) {
+        bhi += 1.0;
+        if (++tries > 30) return 2;
+    }
+    for (int it = 0; it < 200 && bhi - blo > 1e-15 * (1.0 + fabs(blo)); ++it) {
+        double mid = 0.5 * (blo + bhi), gm = G_OF(mid);
+        if (gm > 0.0) blo = mid;
+        else bhi = mid;
+    }
+#undef G_OF
+    double beta = exp(0.5 * (blo + bhi));
+    out[0] = beta;
+    out[1] = species_nu(d, beta, lup) / beta;
+    out[2] = species_nu(d, beta, ldn) / beta;
+    return 0;
+}
