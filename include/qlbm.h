@@ -155,6 +155,39 @@ int qlbm_get_state(qlbm_handle h, double *buf, int ptr_kind);
 int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
 
 /* ------------------------------------------------------------------------
+ * Fermi-Dirac parameters of the local equilibrium (Sec. 2.2, Prop. 1).
+ * ---------------------------------------------------------------------- */
+
+/* qlbm_fd_params -- per site, the parameters of the matrix-valued Fermi-Dirac
+ * distribution whose moments are the site's density matrix rho and internal
+ * energy eps (Eq. DiscrAvr): the analytic eigen-decomposition of rho gives
+ * the occupations n_up/dn = (tr rho +- |S|)/2 and the Bloch axis S/|S| of U;
+ * (beta, mu_up, mu_dn) then solve Eqs. nFDstdOmega and energyFDstdOmega,
+ *   n_s = (2 pi/beta)^(d/2) F_{d/2-1}(beta mu_s),
+ *   tr(rho) eps = (d/2) beta^-1 (2 pi/beta)^(d/2) sum_s F_{d/2}(beta mu_s),
+ * by a Newton iteration per eigenvalue nested in a bracketed Newton iteration
+ * on log beta, in double precision whatever the storage precision.
+ *   beta, mu_up, mu_dn  [N] (any may be NULL);  axis [3][N] (or NULL), zero
+ *   where |S| = 0 (U arbitrary).  Sites where rho is not positive definite
+ *   or no beta fits (eps below the zero-temperature limit) get NaN and are
+ *   counted in *nfail (if not NULL).  All arrays on one side (ptr_kind).
+ * Synchronising. */
+int qlbm_fd_params(qlbm_handle h, double *beta, double *mu_up, double *mu_dn, double *axis,
+                   int64_t *nfail, int ptr_kind);
+
+/* Equilibrium path of qlbm_step.  QLBM_EQ_DIRECT (default): W_i^eq = w_i rho
+ * P_i (Eq. WeqAlgo; "the unitary matrix U ... does not need to be computed").
+ * QLBM_EQ_FD_PARAMS: W_i^eq = w_i U diag(n_up, n_dn) U* P_i (Eq. WeqDiscr)
+ * with U, beta, mu_s recovered per site as in qlbm_fd_params and
+ * n_s = (2 pi/beta)^(d/2) F_{d/2-1}(beta mu_s); it agrees with the direct path
+ * to the accuracy of the solve, and sites without a solution keep rho.
+ * QLBM_FP64 handles only (QLBM_ERR_UNSUPPORTED otherwise); forward stepping
+ * only (qlbm_rollout returns QLBM_ERR_UNSUPPORTED on this path). */
+#define QLBM_EQ_DIRECT 0
+#define QLBM_EQ_FD_PARAMS 1
+int qlbm_set_equilibrium_path(qlbm_handle h, int path);
+
+/* ------------------------------------------------------------------------
  * Reverse mode.  The gradient of an observable J of the state is carried as
  * a cotangent lambda = dJ/dW in the canonical layout double [b][4][N]: for
  * each population, (dJ/df, dJ/ds_x, dJ/ds_y, dJ/ds_z) of its Pauli

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "internal.h"
+#include "fdparams.cuh"
 #include "kernels.cuh"
 
 using namespace qlbm;
@@ -58,6 +59,8 @@ int check_flags(qlbm_ctx *h)
         CK(h, cudaMemsetAsync(h->flags, 0, sizeof(unsigned), h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
     }
+    // FLAG_FD_UNRESOLVED only reports sites that kept rho' = rho on the
+    // Fermi-Dirac path; it is not an error.
     if (f & FLAG_NONFINITE) return fail(h, QLBM_ERR_NONFINITE, "a step met a non-finite moment");
     if (f & FLAG_NONPOSITIVE) return fail(h, QLBM_ERR_NONPOSITIVE_DENSITY, "a step met tr rho <= 0");
     return QLBM_OK;
@@ -283,6 +286,7 @@ void qlbm_destroy(qlbm_handle h)
         if (h->lam[i]) cudaFree(h->lam[i]);
     if (h->dtau_acc) cudaFree(h->dtau_acc);
     if (h->scratch_state) cudaFree(h->scratch_state);
+    if (h->fd_fail) cudaFree(h->fd_fail);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     free_rollout(h);
     delete h;
@@ -330,6 +334,14 @@ int qlbm_step(qlbm_handle h, int64_t nsteps)
 {
     if (!valid(h) || nsteps < 0) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_step: bad argument");
     if (nsteps > 0) h->ro_steps = -1;   // a recorded rollout no longer ends at the current state
+    if (h->eq_path == QLBM_EQ_FD_PARAMS) {
+        for (int64_t i = 0; i < nsteps; ++i) {
+            CK(h, h->ops->step_fd(h, h->parity == 1));
+            h->parity ^= 1;
+            h->t += 1;
+        }
+        return QLBM_OK;
+    }
     if (h->use_graph && nsteps >= 2 * kGraphSteps) {
         if (h->parity == 1) {   // bring the buffer to natural order first
             CK(h, h->ops->step(h, true));
@@ -459,6 +471,8 @@ int qlbm_step_adjoint(qlbm_handle h, const double *lam_next, double *lam, double
 int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval)
 {
     if (!valid(h) || nsteps < 0 || interval < 0) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_rollout: bad argument");
+    if (h->eq_path != QLBM_EQ_DIRECT)
+        return fail(h, QLBM_ERR_UNSUPPORTED, "qlbm_rollout: the reverse mode covers the direct equilibrium path");
     int64_t K = interval;
     if (K == 0) {
         K = 1;
@@ -555,6 +569,46 @@ int qlbm_init_equilibrium_adjoint(qlbm_handle h, const double *rho4, const doubl
     if (g_eps) CK(h, cudaMemcpyAsync(g_eps, ge, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return QLBM_OK;
+}
+
+int qlbm_set_equilibrium_path(qlbm_handle h, int path)
+{
+    if (!valid(h)) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_equilibrium_path: bad handle");
+    if (path != QLBM_EQ_DIRECT && path != QLBM_EQ_FD_PARAMS)
+        return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_equilibrium_path: unknown path");
+    if (path == QLBM_EQ_FD_PARAMS && !h->ops->step_fd)
+        return fail(h, QLBM_ERR_UNSUPPORTED, "the Fermi-Dirac equilibrium path needs QLBM_FP64 storage");
+    h->eq_path = path;
+    h->ro_steps = -1;
+    return QLBM_OK;
+}
+
+int qlbm_fd_params(qlbm_handle h, double *beta, double *mu_up, double *mu_dn, double *axis, int64_t *nfail,
+                   int ptr_kind)
+{
+    if (!valid(h)) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_fd_params: bad handle");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    if (!h->fd_fail) CK(h, cudaMalloc(&h->fd_fail, sizeof(unsigned long long)));
+    CK(h, cudaMemsetAsync(h->fd_fail, 0, sizeof(unsigned long long), h->stream));
+    const size_t N = (size_t)h->g.N;
+    if (ptr_kind == QLBM_HOST) {
+        int rc = ensure_staging(h, 6 * N * sizeof(double));
+        if (rc) return rc;
+        double *b = h->staging, *mu = b + N, *md = mu + N, *ax = md + N;
+        CK(h, h->ops->fd_params(h, beta ? b : nullptr, mu_up ? mu : nullptr, mu_dn ? md : nullptr,
+                                axis ? ax : nullptr));
+        if (beta) CK(h, cudaMemcpyAsync(beta, b, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (mu_up) CK(h, cudaMemcpyAsync(mu_up, mu, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (mu_dn) CK(h, cudaMemcpyAsync(mu_dn, md, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (axis) CK(h, cudaMemcpyAsync(axis, ax, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        CK(h, h->ops->fd_params(h, beta, mu_up, mu_dn, axis));
+    }
+    unsigned long long nf = 0;
+    CK(h, cudaMemcpyAsync(&nf, h->fd_fail, sizeof(nf), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (nfail) *nfail = (int64_t)nf;
+    return check_flags(h);
 }
 
 }  // extern "C"

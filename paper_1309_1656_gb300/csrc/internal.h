@@ -60,6 +60,8 @@ struct qlbm_ctx {
     // CUDA graph of kGraphSteps consecutive steps starting from natural order
     cudaGraphExec_t graph = nullptr;
     int use_graph = 1;
+    int eq_path = 0;                    // QLBM_EQ_DIRECT or QLBM_EQ_FD_PARAMS
+    unsigned long long *fd_fail = nullptr;   // device counter of unresolved sites
     size_t state_bytes() const { return (size_t)b * 4 * (size_t)g.P * elem_bytes; }
     size_t lam_bytes() const { return (size_t)b * 4 * (size_t)g.P * (prec == QLBM_FP64 ? 8 : 4); }
 };
@@ -81,6 +83,9 @@ struct LatticeOps {
     cudaError_t (*lam_export)(qlbm_ctx *h, const void *lam, double *out);
     cudaError_t (*init_adjoint)(qlbm_ctx *h, const double *lam, const double *rho4, const double *u,
                                 const double *eps, double *grho4, double *gu, double *geps);
+    // Fermi-Dirac parameter recovery (side output; FP64 step variant, NULL otherwise)
+    cudaError_t (*fd_params)(qlbm_ctx *h, double *beta, double *mu_up, double *mu_dn, double *axis);
+    cudaError_t (*step_fd)(qlbm_ctx *h, bool odd);
 };
 
 const LatticeOps *lattice_ops_d2q9(int prec);

@@ -5,6 +5,7 @@
 
 #include "internal.h"
 #include "adjoint.cuh"
+#include "fdkernels.cuh"
 #include "kernels.cuh"
 
 namespace qlbm {
@@ -201,11 +202,40 @@ template <int D, class Codec> struct Launchers {
         return cudaGetLastError();
     }
 
+    static cudaError_t fd_params(qlbm_ctx *h, double *beta, double *mu_up, double *mu_dn, double *axis)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        const FdArgs a{h->hc.beta0, h->hc.xi};
+        if (h->parity)
+            k_fd_params<D, Codec, true><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_codec<Codec>(h), a, beta,
+                                                                    mu_up, mu_dn, axis, h->fd_fail);
+        else
+            k_fd_params<D, Codec, false><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_codec<Codec>(h), a, beta,
+                                                                     mu_up, mu_dn, axis, h->fd_fail);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t step_fd(qlbm_ctx *h, bool odd)
+    {
+        if constexpr (std::is_same<Codec, CodecF64>::value) {
+            const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+            const FdArgs a{h->hc.beta0, h->hc.xi};
+            if (odd)
+                k_step_aa_fd<D, true><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_coll<double>(h), a, h->flags);
+            else
+                k_step_aa_fd<D, false><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_coll<double>(h), a, h->flags);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
+
     static const LatticeOps *table()
     {
         static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
                                      &conserved_partial, &adjoint, &push, &copy_natural, &lam_import,
-                                     &lam_export, &init_adjoint};
+                                     &lam_export, &init_adjoint, &fd_params,
+                                     std::is_same<Codec, CodecF64>::value ? &step_fd : nullptr};
         return &t;
     }
 };

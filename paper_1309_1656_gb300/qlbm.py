@@ -32,6 +32,8 @@ QLBM_FP32 = 1
 QLBM_FP16_DEV = 2
 QLBM_HOST = 0
 QLBM_DEVICE = 1
+QLBM_EQ_DIRECT = 0
+QLBM_EQ_FD_PARAMS = 1
 
 PRECISIONS = {"fp64": QLBM_FP64, "fp32": QLBM_FP32, "fp16dev": QLBM_FP16_DEV}
 
@@ -69,6 +71,8 @@ _step_adjoint = _sig("qlbm_step_adjoint", _i, [_vp, _vp, _vp, ctypes.POINTER(_d)
 _rollout = _sig("qlbm_rollout", _i, [_vp, _i64, _i64])
 _rollout_adjoint = _sig("qlbm_rollout_adjoint", _i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i])
 _init_adjoint = _sig("qlbm_init_equilibrium_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i])
+_fd_params = _sig("qlbm_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64), _i])
+_set_eq_path = _sig("qlbm_set_equilibrium_path", _i, [_vp, _i])
 _conserved_static = _sig("qlbm_conserved_static", _i, [_i, ctypes.POINTER(_i64), _d, _vp, _vp, _vp])
 
 
@@ -201,6 +205,19 @@ def qlbm_init_equilibrium_adjoint(h, rho4, u, eps, lam0, g_rho4=None, g_u=None, 
     _check(_init_adjoint(h, *[x[0] for x in p], _kind(*p)), h)
 
 
+def qlbm_fd_params(h, beta=None, mu_up=None, mu_dn=None, axis=None):
+    """Per-site Fermi-Dirac parameters into the given arrays; returns the
+    number of sites without a solution."""
+    p = [_ptr(beta), _ptr(mu_up), _ptr(mu_dn), _ptr(axis)]
+    nf = _i64(0)
+    _check(_fd_params(h, *[x[0] for x in p], ctypes.byref(nf), _kind(*p)), h)
+    return nf.value
+
+
+def qlbm_set_equilibrium_path(h, path):
+    _check(_set_eq_path(h, int(path)), h)
+
+
 def qlbm_conserved_static(lattice, dims, beta0, state, out, stream=None):
     """The eight global averages of qlbm_conserved for a caller-owned device
     state (canonical layout [b][4][N], float64) into a caller-owned device
@@ -289,6 +306,17 @@ class Lattice:
         lam = np.zeros((self.b, 4, self.N))
         g = qlbm_step_adjoint(self.h, np.ascontiguousarray(lam_next, dtype=np.float64), lam)
         return lam, g
+
+    def fd_params(self):
+        beta = np.zeros(self.N)
+        mu_up = np.zeros(self.N)
+        mu_dn = np.zeros(self.N)
+        axis = np.zeros((3, self.N))
+        nfail = qlbm_fd_params(self.h, beta, mu_up, mu_dn, axis)
+        return beta, mu_up, mu_dn, axis, nfail
+
+    def set_equilibrium_path(self, path):
+        qlbm_set_equilibrium_path(self.h, path)
 
     def rollout(self, nsteps, interval=0):
         qlbm_rollout(self.h, nsteps, interval)

@@ -1,0 +1,105 @@
+"""GPU parity of the Fermi-Dirac parameter recovery (Prop. 1) against the
+oracle's independent inversion (its own F_k quadrature and bisection), round
+trips from known parameters, invalid sites, and the step variant that builds
+W^eq through the recovered parameters (Eq. WeqDiscr) against the direct
+equilibrium (Eq. WeqAlgo)."""
+import numpy as np
+import pytest
+
+from paper_1309_1656_gb300 import fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1309_1656_gb300 import qlbm
+    return qlbm
+
+
+@pytest.mark.parametrize("d,dims", [(2, (9, 7, 1)), (3, (5, 4, 3))])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 2e-5)])
+def test_fd_params_vs_oracle(q, oracle_mod, d, dims, prec, tol):
+    beta0 = 1.0
+    fl = fields.random_fields(d, dims, seed=70 + d, umax=0.3)
+    with q.Lattice(d, dims, 0.8, beta0, precision=prec) as lat:
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        lat.step(3)
+        r4, u, eps = lat.moments()
+        beta, mu_up, mu_dn, axis, nfail = lat.fd_params()
+    assert nfail == 0
+    for s in range(r4.shape[1]):
+        rc, ref = oracle_mod.fd_params(d, r4[:, s], eps[s])
+        assert rc == 0
+        assert beta[s] == pytest.approx(ref[0], rel=tol)
+        assert mu_up[s] == pytest.approx(ref[1], rel=tol, abs=tol)
+        assert mu_dn[s] == pytest.approx(ref[2], rel=tol, abs=tol)
+        assert np.allclose(axis[:, s], ref[3:], atol=tol)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_fd_params_round_trip(q, oracle_mod, d):
+    # fields built from known parameters through the oracle's forward map
+    dims = (6, 5, 1) if d == 2 else (4, 3, 3)
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(d + 11)
+    beta = rng.uniform(0.4, 2.5, N)
+    mu_up = rng.uniform(-4.0, 1.5, N)
+    mu_dn = mu_up - rng.uniform(0.0, 1.5, N)
+    mu_dn[:2] = mu_up[:2]                    # degenerate occupations
+    axis = rng.normal(size=(3, N))
+    axis /= np.linalg.norm(axis, axis=0)
+    rho4 = np.zeros((4, N))
+    eps = np.zeros(N)
+    for s in range(N):
+        nu, nd, e = oracle_mod.fd_moments(d, beta[s], mu_up[s], mu_dn[s])
+        rho4[0, s] = nu + nd
+        rho4[1:, s] = (nu - nd) * axis[:, s]
+        eps[s] = e
+    with q.Lattice(d, dims, 0.8, 1.0) as lat:
+        lat.init_equilibrium(rho4, np.zeros((d, N)), eps)
+        b, mu, md, ax, nfail = lat.fd_params()
+    assert nfail == 0
+    assert np.allclose(b, beta, rtol=1e-10)
+    assert np.allclose(mu, mu_up, rtol=1e-9, atol=1e-10)
+    assert np.allclose(md, mu_dn, rtol=1e-9, atol=1e-10)
+    assert np.allclose(ax[:, 2:], axis[:, 2:], atol=1e-9)
+    assert np.all(ax[:, :2] == 0.0)
+
+
+def test_fd_params_invalid_sites(q):
+    d, dims = 3, (4, 2, 2)
+    N = 16
+    fl = fields.random_fields(d, dims, seed=5)
+    fl["rho4"][3, 0] = 1.5 * fl["rho4"][0, 0]     # |S| > n: not positive definite
+    fl["eps"][1] = 1e-7                          # below the degenerate limit
+    with q.Lattice(d, dims, 0.8, 1.0) as lat:
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        b, mu, md, ax, nfail = lat.fd_params()
+    assert nfail == 2
+    assert np.isnan(b[0]) and np.isnan(b[1]) and np.all(np.isfinite(b[2:]))
+
+
+@pytest.mark.parametrize("d,dims", [(2, (33, 17, 1)), (3, (12, 9, 7))])
+def test_fd_equilibrium_path_matches_direct(q, d, dims):
+    fl = fields.random_fields(d, dims, seed=80 + d)
+    out = {}
+    for path in (q.QLBM_EQ_DIRECT, q.QLBM_EQ_FD_PARAMS):
+        with q.Lattice(d, dims, 0.7, 1.0, precision="fp64") as lat:
+            lat.set_equilibrium_path(path)
+            lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+            lat.step(7)
+            lat.sync()
+            out[path] = lat.get_state()
+    a, b = out[q.QLBM_EQ_DIRECT], out[q.QLBM_EQ_FD_PARAMS]
+    assert np.max(np.abs(a - b)) / np.max(np.abs(a)) < 7e-12
+
+
+def test_fd_path_needs_fp64(q):
+    with q.Lattice(2, (8, 8, 1), 0.8, 1.0, precision="fp32") as lat:
+        with pytest.raises(q.QLBMError) as e:
+            lat.set_equilibrium_path(q.QLBM_EQ_FD_PARAMS)
+        assert e.value.code == q.QLBM_ERR_UNSUPPORTED
