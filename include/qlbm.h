@@ -175,6 +175,17 @@ int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
 int qlbm_fd_params(qlbm_handle h, double *beta, double *mu_up, double *mu_dn, double *axis,
                    int64_t *nfail, int ptr_kind);
 
+/* qlbm_fd_params_adjoint -- reverse mode of qlbm_fd_params at the current
+ * state, by the implicit-function rule: with p = (beta, beta mu_up,
+ * beta mu_dn) solving G(p; n_up, n_dn, tr(rho) eps) = 0 (the two equations
+ * above), dp/d(n_up, n_dn, tr(rho) eps) = (dG/dp)^-1.  Given the cotangents
+ * g_beta, g_mu_up, g_mu_dn [N] and g_axis [3][N] (any may be NULL = 0) of
+ * the outputs, writes lam = dJ/dW [b][4][N] through n_up/dn = (tr rho +-
+ * |S|)/2, axis = S/|S| and the moments of Eq. DiscrAvr.  Sites without a
+ * solution get lam = 0.  All arrays on one side (ptr_kind).  Synchronising. */
+int qlbm_fd_params_adjoint(qlbm_handle h, const double *g_beta, const double *g_mu_up,
+                           const double *g_mu_dn, const double *g_axis, double *lam, int ptr_kind);
+
 /* Equilibrium path of qlbm_step.  QLBM_EQ_DIRECT (default): W_i^eq = w_i rho
  * P_i (Eq. WeqAlgo; "the unitary matrix U ... does not need to be computed").
  * QLBM_EQ_FD_PARAMS: W_i^eq = w_i U diag(n_up, n_dn) U* P_i (Eq. WeqDiscr)

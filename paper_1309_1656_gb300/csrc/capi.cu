@@ -611,4 +611,29 @@ int qlbm_fd_params(qlbm_handle h, double *beta, double *mu_up, double *mu_dn, do
     return check_flags(h);
 }
 
+int qlbm_fd_params_adjoint(qlbm_handle h, const double *g_beta, const double *g_mu_up, const double *g_mu_dn,
+                           const double *g_axis, double *lam, int ptr_kind)
+{
+    if (!valid(h) || !lam) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_fd_params_adjoint: bad argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    if (ptr_kind == QLBM_DEVICE) {
+        CK(h, h->ops->fd_params_adjoint(h, g_beta, g_mu_up, g_mu_dn, g_axis, lam));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return check_flags(h);
+    }
+    const size_t N = (size_t)h->g.N, ld = (size_t)h->b * 4 * N;
+    int rc = ensure_staging(h, (6 * N + ld) * sizeof(double));
+    if (rc) return rc;
+    double *gb = h->staging, *gu = gb + N, *gd = gu + N, *ga = gd + N, *l = ga + 3 * N;
+    if (g_beta) CK(h, cudaMemcpyAsync(gb, g_beta, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (g_mu_up) CK(h, cudaMemcpyAsync(gu, g_mu_up, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (g_mu_dn) CK(h, cudaMemcpyAsync(gd, g_mu_dn, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (g_axis) CK(h, cudaMemcpyAsync(ga, g_axis, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, h->ops->fd_params_adjoint(h, g_beta ? gb : nullptr, g_mu_up ? gu : nullptr, g_mu_dn ? gd : nullptr,
+                                    g_axis ? ga : nullptr, l));
+    CK(h, cudaMemcpyAsync(lam, l, ld * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return check_flags(h);
+}
+
 }  // extern "C"

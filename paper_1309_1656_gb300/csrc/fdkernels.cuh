@@ -51,6 +51,97 @@ k_fd_params(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec cod
     if (p.status != 0) atomicAdd(nfail, 1ull);
 }
 
+// Reverse mode of qlbm_fd_params by the implicit-function rule.  The
+// parameters p = (beta, nu_up, nu_dn), nu = beta mu, solve G(p; m) = 0 with
+// m = (n_up, n_dn, E = n eps) and
+//   G_s = A F_{h-1}(nu_s) - n_s,  G_3 = h beta^-1 A sum_s F_h(nu_s) - E,  A = (2 pi/beta)^h,
+// so dp/dm = J^-1 with J = dG/dp (dG/dm = -1), and a cotangent pbar of p
+// gives mbar = J^-T pbar.  Then n_up/dn = (n +- |S|)/2, axis = S/|S| and
+// E = xi^2/2 (E2 - |J_lat|^2/n) (J_lat = sum i f, E2 = sum |i|^2 f) carry it
+// to the populations: lambda_f,i = nbar + i.Jbar + |i|^2 E2bar, lambda_s,i = Sbar.
+// Output: the cotangent of the current state in the canonical layout.
+template <int D, class Codec, bool SWAPPED>
+__global__ void __launch_bounds__(kStepBlock)
+k_fd_params_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec codec, FdArgs a,
+                    const double *__restrict__ gbeta, const double *__restrict__ gmu_up,
+                    const double *__restrict__ gmu_dn, const double *__restrict__ gaxis,
+                    double *__restrict__ lam)
+{
+    using R = typename Codec::R;
+    constexpr int Q = Lattice<D>::Q;
+    constexpr double h = 0.5 * D;
+    SiteIdx si;
+    if (!site_of_block(g, si)) return;
+    R f[Q], sx[Q], sy[Q], sz[Q];
+    gather<D, Codec, SWAPPED>(pl, g, si, codec, f, sx, sy, sz);
+    double fd[Q], xd[Q], yd[Q], zd[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cls = cnorm2<D>(q);
+        fd[q] = codec.to_double(f[q], 0, cls);
+        xd[q] = codec.to_double(sx[q], 1, cls);
+        yd[q] = codec.to_double(sy[q], 2, cls);
+        zd[q] = codec.to_double(sz[q], 3, cls);
+    }
+    const SiteMoments<D, double> m = site_moments<D, double>(fd, xd, yd, zd);
+    const double jj = m.jx * m.jx + m.jy * m.jy + m.jz * m.jz;
+    const double eps = 0.5 * a.xi * a.xi * (m.e2n - jj);
+    const FdParams p = fd_params_site<D>(m.n, m.Sx, m.Sy, m.Sz, eps);
+    const int64_t N = g.N, s = si.s;
+    double nbar = 0.0, Sbx = 0.0, Sby = 0.0, Sbz = 0.0, Jbx = 0.0, Jby = 0.0, Jbz = 0.0, E2bar = 0.0;
+    if (p.status == 0) {
+        const double beta = p.beta, nu1 = beta * p.mu_up, nu2 = beta * p.mu_dn;
+        const double bb = gbeta ? gbeta[s] : 0.0, b1 = gmu_up ? gmu_up[s] : 0.0, b2 = gmu_dn ? gmu_dn[s] : 0.0;
+        // cotangent of (beta, nu_up, nu_dn)
+        const double pb0 = bb - (b1 * p.mu_up + b2 * p.mu_dn) / beta, pb1 = b1 / beta, pb2 = b2 / beta;
+        const double A = pow(kTwoPi / beta, h);
+        const double F1 = fd_hm1<D>(nu1), F2 = fd_hm1<D>(nu2);
+        const double Fh = fd_h<D>(nu1) + fd_h<D>(nu2);
+        // J rows: G1, G2, G3; columns: beta, nu_up, nu_dn
+        const double J00 = -h / beta * A * F1, J01 = A * fd_hm2<D>(nu1);
+        const double J10 = -h / beta * A * F2, J12 = A * fd_hm2<D>(nu2);
+        const double J20 = -(h + 1.0) / beta * h / beta * A * Fh, J21 = h / beta * A * F1, J22 = h / beta * A * F2;
+        // solve J^T mbar = pbar:
+        //   J00 m0 + J10 m1 + J20 m2 = pb0
+        //   J01 m0 +            J21 m2 = pb1
+        //              J12 m1 + J22 m2 = pb2
+        // m0 = (pb1 - J21 m2)/J01, m1 = (pb2 - J22 m2)/J12, substitute into the first
+        const double den = J20 - J00 * J21 / J01 - J10 * J22 / J12;
+        const double m2 = (pb0 - J00 * pb1 / J01 - J10 * pb2 / J12) / den;
+        const double m0 = (pb1 - J21 * m2) / J01, m1 = (pb2 - J22 * m2) / J12;
+        nbar = 0.5 * (m0 + m1);
+        const double nS = sqrt(m.Sx * m.Sx + m.Sy * m.Sy + m.Sz * m.Sz);
+        if (nS > 0.0) {
+            const double sbar = 0.5 * (m0 - m1);
+            double ax = 0.0, ay = 0.0, az = 0.0;
+            if (gaxis) {
+                ax = gaxis[s];
+                ay = gaxis[N + s];
+                az = gaxis[2 * N + s];
+            }
+            const double adot = ax * p.ax + ay * p.ay + az * p.az;
+            Sbx = sbar * p.ax + (ax - adot * p.ax) / nS;
+            Sby = sbar * p.ay + (ay - adot * p.ay) / nS;
+            Sbz = sbar * p.az + (az - adot * p.az) / nS;
+        }
+        // E = xi^2/2 (E2 - |J_lat|^2 / n): its cotangent m2
+        const double c = 0.5 * a.xi * a.xi * m2;
+        E2bar = c;
+        Jbx = -2.0 * c * m.jx;
+        Jby = -2.0 * c * m.jy;
+        Jbz = -2.0 * c * m.jz;
+        nbar += c * jj;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        double *o = lam + (int64_t)(4 * q) * N + s;
+        o[0] = nbar + cx<D>(q) * Jbx + cy<D>(q) * Jby + cz<D>(q) * Jbz + cnorm2<D>(q) * E2bar;
+        o[N] = Sbx;
+        o[2 * N] = Sby;
+        o[3 * N] = Sbz;
+    }
+}
+
 // Collision whose equilibrium density matrix is rebuilt from the recovered
 // parameters: rho' = U diag(n_up', n_dn') U*, n_s' = (2 pi/beta)^h F_{h-1}(beta mu_s)
 // (Eq. WeqDiscr), i.e. n' = n_up' + n_dn', S' = (n_up' - n_dn') axis; u and

@@ -86,6 +86,8 @@ struct LatticeOps {
     // Fermi-Dirac parameter recovery (side output; FP64 step variant, NULL otherwise)
     cudaError_t (*fd_params)(qlbm_ctx *h, double *beta, double *mu_up, double *mu_dn, double *axis);
     cudaError_t (*step_fd)(qlbm_ctx *h, bool odd);
+    cudaError_t (*fd_params_adjoint)(qlbm_ctx *h, const double *gbeta, const double *gmu_up,
+                                     const double *gmu_dn, const double *gaxis, double *lam);
 };
 
 const LatticeOps *lattice_ops_d2q9(int prec);

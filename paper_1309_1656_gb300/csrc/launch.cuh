@@ -230,12 +230,27 @@ template <int D, class Codec> struct Launchers {
         }
     }
 
+    static cudaError_t fd_params_adjoint(qlbm_ctx *h, const double *gbeta, const double *gmu_up,
+                                         const double *gmu_dn, const double *gaxis, double *lam)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        const FdArgs a{h->hc.beta0, h->hc.xi};
+        if (h->parity)
+            k_fd_params_adjoint<D, Codec, true><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_codec<Codec>(h), a,
+                                                                            gbeta, gmu_up, gmu_dn, gaxis, lam);
+        else
+            k_fd_params_adjoint<D, Codec, false><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_codec<Codec>(h), a,
+                                                                             gbeta, gmu_up, gmu_dn, gaxis, lam);
+        return cudaGetLastError();
+    }
+
     static const LatticeOps *table()
     {
         static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
                                      &conserved_partial, &adjoint, &push, &copy_natural, &lam_import,
                                      &lam_export, &init_adjoint, &fd_params,
-                                     std::is_same<Codec, CodecF64>::value ? &step_fd : nullptr};
+                                     std::is_same<Codec, CodecF64>::value ? &step_fd : nullptr,
+                                     &fd_params_adjoint};
         return &t;
     }
 };

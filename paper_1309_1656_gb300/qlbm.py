@@ -72,6 +72,7 @@ _rollout = _sig("qlbm_rollout", _i, [_vp, _i64, _i64])
 _rollout_adjoint = _sig("qlbm_rollout_adjoint", _i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i])
 _init_adjoint = _sig("qlbm_init_equilibrium_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i])
 _fd_params = _sig("qlbm_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64), _i])
+_fd_params_adjoint = _sig("qlbm_fd_params_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
 _set_eq_path = _sig("qlbm_set_equilibrium_path", _i, [_vp, _i])
 _conserved_static = _sig("qlbm_conserved_static", _i, [_i, ctypes.POINTER(_i64), _d, _vp, _vp, _vp])
 
@@ -212,6 +213,12 @@ def qlbm_fd_params(h, beta=None, mu_up=None, mu_dn=None, axis=None):
     nf = _i64(0)
     _check(_fd_params(h, *[x[0] for x in p], ctypes.byref(nf), _kind(*p)), h)
     return nf.value
+
+
+def qlbm_fd_params_adjoint(h, lam, g_beta=None, g_mu_up=None, g_mu_dn=None, g_axis=None):
+    """Cotangent of the current state (into lam) from those of the FD parameters."""
+    p = [_ptr(g_beta), _ptr(g_mu_up), _ptr(g_mu_dn), _ptr(g_axis), _ptr(lam)]
+    _check(_fd_params_adjoint(h, *[x[0] for x in p], _kind(*p)), h)
 
 
 def qlbm_set_equilibrium_path(h, path):
