@@ -293,6 +293,40 @@ def bench_ours(args):
         del lat, lam_T, lam_0
         torch.cuda.synchronize()
 
+    # Fermi-Dirac parameter recovery (side output, FP64 solve) and the FP64
+    # step variant whose equilibrium goes through the recovered parameters
+    fdp = None
+    if args.fd_params and rank == 0:
+        lat = qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision="fp64", stream=stream.cuda_stream)
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        lat.step(4)
+        outs = [torch.empty((N,), dtype=torch.float64, device="cuda") for _ in range(3)]
+        ax = torch.empty((3, N), dtype=torch.float64, device="cuda")
+        qlbm.qlbm_fd_params(lat.h, *outs, ax)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        nfail = qlbm.qlbm_fd_params(lat.h, *outs, ax)
+        ev[1].record(stream)
+        lat.set_equilibrium_path(qlbm.QLBM_EQ_FD_PARAMS)
+        ns = 10
+        lat.step(2)
+        lat.sync()
+        ev[2].record(stream)
+        lat.step(ns)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        t_fd = ev[0].elapsed_time(ev[1])
+        t_step = ev[2].elapsed_time(ev[3]) / ns
+        fdp = {"fd_params_ms": round(t_fd, 3), "fd_params_msites_per_s": round(N / t_fd / 1e3, 1),
+               "fd_path_step_ms": round(t_step, 3), "fd_path_mlups": round(N / t_step / 1e3, 1),
+               "unresolved_sites": nfail, "beta_median": float(outs[0].median()),
+               "note": "FP64 per-site eigen-decomposition + nested Newton (Prop. 1); cost reported "
+                       "separately, the paper's step does not need it"}
+        lat.close()
+        del outs, ax
+        torch.cuda.synchronize()
+
     # end-to-end through the C ABI with pinned host buffers
     e2e = None
     if "fp32" in results and not args.no_e2e:
@@ -375,6 +409,8 @@ def bench_ours(args):
         line["e2e"] = e2e
     if adj:
         line["adjoint"] = adj
+    if fdp:
+        line["fd_params"] = fdp
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -498,6 +534,8 @@ def main():
     ap.add_argument("--error-growth", type=int, default=0,
                     help="also run FP64/FP32/FP16 side by side for this many steps and report errors")
     ap.add_argument("--error-every", type=int, default=1000)
+    ap.add_argument("--no-fd-params", dest="fd_params", action="store_false",
+                    help="skip timing the Fermi-Dirac parameter recovery")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

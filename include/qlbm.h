@@ -154,6 +154,16 @@ int qlbm_conserved(qlbm_handle h, double *out);
 int qlbm_get_state(qlbm_handle h, double *buf, int ptr_kind);
 int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
 
+/* qlbm_set_magnetic_field -- adds the Vlasov commutator of an external
+ * magnetic field, -i[mu sigma.B, W] (Sec. 5, Eq. sigmaB_comm), "to the
+ * collision operator": integrated exactly over each time step it is
+ * W_i -> U W_i U*, U = exp(-i mu dt sigma.B), a rotation of every Bloch
+ * vector s_i by 2 mu |B| dt about B.  The field is uniform; it commutes with
+ * the SU(2)-covariant collision, so it is applied to the post-collision
+ * populations in the same fused kernel.  mu = 0 or B = 0 switches it off.
+ * Applies to qlbm_step, qlbm_rollout and the reverse mode. */
+int qlbm_set_magnetic_field(qlbm_handle h, double mu, const double B[3]);
+
 /* ------------------------------------------------------------------------
  * Fermi-Dirac parameters of the local equilibrium (Sec. 2.2, Prop. 1).
  * ---------------------------------------------------------------------- */
@@ -174,6 +184,16 @@ int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
  * Synchronising. */
 int qlbm_fd_params(qlbm_handle h, double *beta, double *mu_up, double *mu_dn, double *axis,
                    int64_t *nfail, int ptr_kind);
+
+/* qlbm_init_fd_params -- equilibrium initial state from physical Fermi-Dirac
+ * parameters (Sec. 2.2), as the paper sets up its Riemann problem: per site
+ * n_s = (2 pi/beta)^(d/2) F_{d/2-1}(beta mu_s) (Eq. nFDstdOmega), eps from
+ * Eq. energyFDstdOmega, rho = U diag(n_up, n_dn) U* with Bloch axis `axis`
+ * (unit vector, or zero), then W_i = W_i^eq(rho, u, eps) (Eq. WeqAlgo).
+ *   beta, mu_up, mu_dn [N];  axis [3][N];  u [d][N];  one side (ptr_kind).
+ * Resets the step counter. */
+int qlbm_init_fd_params(qlbm_handle h, const double *beta, const double *mu_up,
+                        const double *mu_dn, const double *axis, const double *u, int ptr_kind);
 
 /* qlbm_fd_params_adjoint -- reverse mode of qlbm_fd_params at the current
  * state, by the implicit-function rule: with p = (beta, beta mu_up,

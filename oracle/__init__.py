@@ -94,6 +94,8 @@ def _load():
         lib.oracle_conserved.argtypes = [_i, _pi64, _d, _pd, _pd]
         lib.oracle_adjoint_step.restype = _i
         lib.oracle_adjoint_step.argtypes = [_i, _pi64, _d, _d, _d, _pd, _pd, _pd, _pd, _i]
+        lib.oracle_set_field.restype = None
+        lib.oracle_set_field.argtypes = [_d, _d, _d, _d]
         lib.oracle_fd.restype = _d
         lib.oracle_fd.argtypes = [_d, _d]
         lib.oracle_fd_moments.restype = _i
@@ -253,3 +255,8 @@ def fd_params(d, rho4, eps):
     out = np.zeros(6)
     rc = _load().oracle_fd_params(int(d), _ptr(r), float(eps), _ptr(out))
     return rc, out
+
+
+def set_field(mu, B):
+    """Uniform external magnetic field for the following runs (mu = 0: off)."""
+    _load().oracle_set_field(float(mu), float(B[0]), float(B[1]), float(B[2]))

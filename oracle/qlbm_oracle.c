@@ -279,6 +279,54 @@ static void site_collide(const lattice *L, double omega, const mat2 *W, mat2 *Wc
 }
 
 /* ------------------------------------------------------------------------- */
+/* External magnetic field (Sec. 5, Eq. sigmaB_comm): the term                */
+/* -i[mu sigma.B, W] added to the collision, integrated exactly over one     */
+/* time step: W -> U W U*, U = exp(-i mu dt sigma.B)                          */
+/*   = cos(phi) 1 - i sin(phi) (b.sigma), phi = mu dt |B|, b = B/|B|.          */
+/* Off unless oracle_set_field is called with mu |B| != 0.                    */
+/* ------------------------------------------------------------------------- */
+static double field_mu = 0.0, field_B[3] = {0.0, 0.0, 0.0};
+
+void oracle_set_field(double mu, double Bx, double By, double Bz)
+{
+    field_mu = mu;
+    field_B[0] = Bx;
+    field_B[1] = By;
+    field_B[2] = Bz;
+}
+
+static int field_unitary(double dt, mat2 *U)
+{
+    double nb = sqrt(field_B[0] * field_B[0] + field_B[1] * field_B[1] + field_B[2] * field_B[2]);
+    if (!(nb > 0.0) || field_mu == 0.0) return 0;
+    double phi = field_mu * dt * nb, c = cos(phi), s = sin(phi);
+    double bx = field_B[0] / nb, by = field_B[1] / nb, bz = field_B[2] / nb;
+    /* b.sigma = [[bz, bx - i by], [bx + i by, -bz]] */
+    U->m[0][0] = c - I * s * bz;
+    U->m[0][1] = -I * s * (bx - I * by);
+    U->m[1][0] = -I * s * (bx + I * by);
+    U->m[1][1] = c + I * s * bz;
+    return 1;
+}
+
+/* A -> X A Y for 2x2 complex matrices */
+static void mat_sandwich(const mat2 *X, mat2 *A, const mat2 *Y)
+{
+    mat2 T, R;
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) T.m[j][k] = X->m[j][0] * A->m[0][k] + X->m[j][1] * A->m[1][k];
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) R.m[j][k] = T.m[j][0] * Y->m[0][k] + T.m[j][1] * Y->m[1][k];
+    *A = R;
+}
+
+static void mat_adjoint(const mat2 *A, mat2 *B)
+{
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) B->m[j][k] = conj(A->m[k][j]);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Lattice helpers                                                            */
 /* ------------------------------------------------------------------------- */
 typedef struct { int64_t nx, ny, nz, N; } grid;
@@ -346,15 +394,20 @@ int oracle_max_threads(int nthreads) { return set_threads(nthreads); }
 /* One full step t -> t + dt on matrix states: collision at every cell
    (Eq. CollisionStep), then W_i(x + dt e_i, t + dt) = W_i^coll(x, t)
    (Eq. TransportStep) with dt xi = dx, i.e. one cell along i, periodic. */
-static void step_matrix(const lattice *L, const grid *G, double omega,
+static void step_matrix(const lattice *L, const grid *G, double omega, double dt,
                         const mat2 *src, mat2 *dst)
 {
     int64_t N = G->N;
     int b = L->b;
+    mat2 U, Ud;
+    int field = field_unitary(dt, &U);
+    if (field) mat_adjoint(&U, &Ud);
 #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < N; ++s) {
         mat2 Wc[QMAX];
         site_collide(L, omega, &src[s * b], Wc);
+        if (field)
+            for (int i = 0; i < b; ++i) mat_sandwich(&U, &Wc[i], &Ud);   /* W -> U W U* */
         for (int i = 0; i < b; ++i) {
             int64_t t = shift_site(G, s, L->idx[i][0], L->idx[i][1], L->idx[i][2]);
             dst[t * b + i] = Wc[i];
@@ -379,7 +432,7 @@ int oracle_run_matrix(int d, const int64_t *dims, double tau, double beta0, doub
     if (!tmp) return -2;
     mat2 *src = a, *dst = tmp;
     for (int64_t n = 0; n < nsteps; ++n) {
-        step_matrix(&L, &G, omega, src, dst);
+        step_matrix(&L, &G, omega, dt, src, dst);
         mat2 *t = src; src = dst; dst = t;
     }
     if (src != a) memcpy(a, src, bytes);
@@ -631,6 +684,9 @@ int oracle_adjoint_step(int d, const int64_t *dims, double tau, double beta0, do
     int b = L.b;
     double omega = dt / tau, dom_dtau = -dt / (tau * tau);
     double total = 0.0;
+    mat2 U, Ud;
+    int field = field_unitary(dt, &U);
+    if (field) mat_adjoint(&U, &Ud);
 #pragma omp parallel for schedule(static) reduction(+ : total)
     for (int64_t s = 0; s < N; ++s) {
         mat2 W[QMAX], Lp[QMAX], Lo[QMAX];
@@ -644,6 +700,8 @@ int oracle_adjoint_step(int d, const int64_t *dims, double tau, double beta0, do
             Lp[i].m[1][1] = l[0] - l[3 * N];
             Lp[i].m[0][1] = l[N] - I * l[2 * N];
             Lp[i].m[1][0] = l[N] + I * l[2 * N];
+            /* W_rot = U W_c U*: dJ = tr(L' U dW_c U*) = tr(U* L' U dW_c) */
+            if (field) mat_sandwich(&Ud, &Lp[i], &U);
         }
         double part = 0.0;
         site_collide_adjoint(&L, omega, dom_dtau, W, Lp, Lo, &part);

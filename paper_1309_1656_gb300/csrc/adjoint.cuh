@@ -132,7 +132,18 @@ template <typename R> struct MuMom {
     }
 };
 
-template <int D, class Codec, int q>
+// Cotangent of the pre-rotation spins: mu_s <- R^T mu_s (the field term
+// rotates the post-collision spins by R).
+template <typename R>
+__device__ __forceinline__ void unrotate(R &mx, R &my, R &mz, const R (&rot)[9])
+{
+    const R x = mx, y = my, z = mz;
+    mx = rot[0] * x + rot[3] * y + rot[6] * z;
+    my = rot[1] * x + rot[4] * y + rot[7] * z;
+    mz = rot[2] * x + rot[5] * y + rot[8] * z;
+}
+
+template <int D, class Codec, int q, bool MAG>
 __device__ __forceinline__ void adj_accumulate(const Planes<typename Codec::S, Lattice<D>::Q> &st,
                                                const Planes<typename Codec::R, Lattice<D>::Q> &lin,
                                                const Grid &g, const SiteIdx &si, const Codec &codec,
@@ -147,7 +158,8 @@ __device__ __forceinline__ void adj_accumulate(const Planes<typename Codec::S, L
     const R sy = codec.load(st.p[4 * q + 2][si.s]);
     const R sz = codec.load(st.p[4 * q + 3][si.s]);
     const int s = neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q));
-    const R mf = lin.p[4 * q][s], mx = lin.p[4 * q + 1][s], my = lin.p[4 * q + 2][s], mz = lin.p[4 * q + 3][s];
+    R mf = lin.p[4 * q][s], mx = lin.p[4 * q + 1][s], my = lin.p[4 * q + 2][s], mz = lin.p[4 * q + 3][s];
+    if constexpr (MAG) unrotate(mx, my, mz, k.rot);
     fw[0] += f;
     fw[1] += sx;
     fw[2] += sy;
@@ -164,7 +176,7 @@ __device__ __forceinline__ void adj_accumulate(const Planes<typename Codec::S, L
     Bz.template add<D, q>(w * mz);
 }
 
-template <int D, class Codec, int q>
+template <int D, class Codec, int q, bool MAG>
 struct AdjLoop {
     static __device__ __forceinline__ void run(const Planes<typename Codec::S, Lattice<D>::Q> &st,
                                                const Planes<typename Codec::R, Lattice<D>::Q> &lin,
@@ -174,11 +186,11 @@ struct AdjLoop {
                                                MuMom<typename Codec::R> &Bx, MuMom<typename Codec::R> &By,
                                                MuMom<typename Codec::R> &Bz)
     {
-        adj_accumulate<D, Codec, q>(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
-        AdjLoop<D, Codec, q + 1>::run(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
+        adj_accumulate<D, Codec, q, MAG>(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
+        AdjLoop<D, Codec, q + 1, MAG>::run(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
     }
 };
-template <int D, class Codec> struct AdjLoop<D, Codec, Lattice<D>::Q> {
+template <int D, class Codec, bool MAG> struct AdjLoop<D, Codec, Lattice<D>::Q, MAG> {
     static __device__ __forceinline__ void run(const Planes<typename Codec::S, Lattice<D>::Q> &,
                                                const Planes<typename Codec::R, Lattice<D>::Q> &,
                                                const Grid &, const SiteIdx &, const Codec &,
@@ -202,7 +214,7 @@ template <int D, class Codec> struct AdjLoop<D, Codec, Lattice<D>::Q> {
 // are known.  Pass 2 re-reads mu (cache hits; the index carries the
 // run-time zero so the compiler does not keep pass 1's values live) and
 // writes lambda^n.
-template <int D, class Codec>
+template <int D, class Codec, bool MAG>
 __global__ void __launch_bounds__(kAdjBlock, Codec::MIN_BLOCKS)
 k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typename Codec::R, Lattice<D>::Q> lin,
           const Planes<typename Codec::R, Lattice<D>::Q> lout, Grid g, Coll<typename Codec::R> k,
@@ -222,7 +234,7 @@ k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typena
         Bx.zero();
         By.zero();
         Bz.zero();
-        AdjLoop<D, Codec, 0>::run(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
+        AdjLoop<D, Codec, 0, MAG>::run(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
         // forward moments
         const R dn = DEV ? fw[0] : fw[0] - R(1);
         const R n = DEV ? R(1) + fw[0] : fw[0];
@@ -283,8 +295,9 @@ k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typena
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int s = neighbour(g, s2, cx<D>(q), cy<D>(q), cz<D>(q));
-            const R mf = lin.p[4 * q][s], mx = lin.p[4 * q + 1][s], my = lin.p[4 * q + 2][s],
-                    mz = lin.p[4 * q + 3][s];
+            R mf = lin.p[4 * q][s], mx = lin.p[4 * q + 1][s], my = lin.p[4 * q + 2][s],
+              mz = lin.p[4 * q + 3][s];
+            if constexpr (MAG) unrotate(mx, my, mz, k.rot);
             lout.p[4 * q][s2.s] = omc * mf + nbar +
                                   (cx<D>(q) * Jbx2 + cy<D>(q) * Jby2 + cz<D>(q) * Jbz2) + cnorm2<D>(q) * Eb;
             lout.p[4 * q + 1][s2.s] = omc * mx + Sbx;
@@ -298,7 +311,7 @@ k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typena
 
 // Two-buffer forward step (push): src and dst in natural order.  Used to
 // recompute the states inside a checkpoint segment.
-template <int D, class Codec>
+template <int D, class Codec, bool MAG>
 __global__ void __launch_bounds__(kStepBlock, Codec::MIN_BLOCKS)
 k_step_push(const Planes<typename Codec::S, Lattice<D>::Q> src, const Planes<typename Codec::S, Lattice<D>::Q> dst,
             Grid g, Coll<typename Codec::R> k, Codec codec, unsigned *__restrict__ flags)
@@ -314,6 +327,7 @@ k_step_push(const Planes<typename Codec::S, Lattice<D>::Q> src, const Planes<typ
         flag = collide_dev<D>(f, sx, sy, sz, k);
     else
         flag = collide<D, R>(f, sx, sy, sz, k);
+    if constexpr (MAG) rotate_spins<D, R>(sx, sy, sz, k.rot);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int s = neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q));

@@ -571,6 +571,60 @@ int qlbm_init_equilibrium_adjoint(qlbm_handle h, const double *rho4, const doubl
     return QLBM_OK;
 }
 
+int qlbm_init_fd_params(qlbm_handle h, const double *beta, const double *mu_up, const double *mu_dn,
+                        const double *axis, const double *u, int ptr_kind)
+{
+    if (!valid(h) || !beta || !mu_up || !mu_dn || !axis || !u)
+        return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_init_fd_params: null argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    const size_t N = (size_t)h->g.N;
+    if (ptr_kind == QLBM_HOST) {
+        int rc = ensure_staging(h, (6 + (size_t)h->d) * N * sizeof(double));
+        if (rc) return rc;
+        double *b = h->staging, *mu = b + N, *md = mu + N, *ax = md + N, *uu = ax + 3 * N;
+        CK(h, cudaMemcpyAsync(b, beta, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(mu, mu_up, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(md, mu_dn, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(ax, axis, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(uu, u, (size_t)h->d * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, h->ops->init_fd(h, b, mu, md, ax, uu));
+        CK(h, cudaStreamSynchronize(h->stream));
+    } else {
+        CK(h, h->ops->init_fd(h, beta, mu_up, mu_dn, axis, u));
+    }
+    h->parity = 0;
+    h->t = 0;
+    h->ro_steps = -1;
+    return QLBM_OK;
+}
+
+int qlbm_set_magnetic_field(qlbm_handle h, double mu, const double B[3])
+{
+    if (!valid(h) || !B) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_magnetic_field: bad argument");
+    const double nb = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    if (!(nb == nb) || !(mu == mu)) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_magnetic_field: NaN");
+    double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    int mag = 0;
+    if (nb > 0.0 && mu != 0.0) {
+        // rotation by theta = 2 mu |B| dt about B/|B| (Rodrigues)
+        const double th = 2.0 * mu * nb * h->dt, c = cos(th), s = sin(th), C = 1.0 - c;
+        const double x = B[0] / nb, y = B[1] / nb, z = B[2] / nb;
+        const double r[9] = {c + x * x * C,     x * y * C - z * s, x * z * C + y * s,
+                             y * x * C + z * s, c + y * y * C,     y * z * C - x * s,
+                             z * x * C - y * s, z * y * C + x * s, c + z * z * C};
+        for (int i = 0; i < 9; ++i) rot[i] = r[i];
+        mag = 1;
+    }
+    for (int i = 0; i < 9; ++i) h->rot[i] = rot[i];
+    h->mag = mag;
+    if (h->graph) {   // the captured launches carry the old field
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->ro_steps = -1;
+    return QLBM_OK;
+}
+
 int qlbm_set_equilibrium_path(qlbm_handle h, int path)
 {
     if (!valid(h)) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_equilibrium_path: bad handle");

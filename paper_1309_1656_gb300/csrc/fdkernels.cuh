@@ -142,6 +142,43 @@ k_fd_params_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, C
     }
 }
 
+// Equilibrium initial state from physical Fermi-Dirac parameters: per site
+// n_s = (2 pi/beta)^h F_{h-1}(beta mu_s) (Eq. nFDstdOmega),
+// eps = h beta^-1 sum_s F_h(beta mu_s) / sum_s F_{h-1}(beta mu_s)
+// (Eq. energyFDstdOmega), rho = U diag(n_up, n_dn) U* with U's Bloch axis
+// `axis` (tr rho = n_up + n_dn, S = (n_up - n_dn) axis), and W_i = W_i^eq of
+// Eq. WeqAlgo with the given velocity.
+template <int D, class Codec>
+__global__ void __launch_bounds__(kStepBlock)
+k_init_fd(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, InitConsts ic, Codec codec,
+          const double *__restrict__ beta, const double *__restrict__ mu_up, const double *__restrict__ mu_dn,
+          const double *__restrict__ axis, const double *__restrict__ u)
+{
+    constexpr int Q = Lattice<D>::Q;
+    constexpr double h = 0.5 * D;
+    SiteIdx si;
+    if (!site_of_block(g, si)) return;
+    const int64_t N = g.N, s = si.s;
+    const double b = beta[s], nu1 = b * mu_up[s], nu2 = b * mu_dn[s];
+    const double pre = pow(kTwoPi / b, h);
+    const double F1 = fd_hm1<D>(nu1), F2 = fd_hm1<D>(nu2);
+    const double nup = pre * F1, ndn = pre * F2;
+    const double n = nup + ndn;
+    const double e = h / b * (fd_h<D>(nu1) + fd_h<D>(nu2)) / (F1 + F2);
+    const double Sx = (nup - ndn) * axis[s], Sy = (nup - ndn) * axis[N + s], Sz = (nup - ndn) * axis[2 * N + s];
+    const double jx = u[s] / ic.xi, jy = u[N + s] / ic.xi, jz = (D == 3) ? u[2 * N + s] / ic.xi : 0.0;
+    const double be = ic.beta0 * e;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int cls = cnorm2<D>(q);
+        const double wp = ic.w[cls] * poly_P_d<D>(ic, q, jx, jy, jz, be);
+        pl.p[4 * q][s] = codec.from_double(wp * n, 0, cls);
+        pl.p[4 * q + 1][s] = codec.from_double(wp * Sx, 1, cls);
+        pl.p[4 * q + 2][s] = codec.from_double(wp * Sy, 2, cls);
+        pl.p[4 * q + 3][s] = codec.from_double(wp * Sz, 3, cls);
+    }
+}
+
 // Collision whose equilibrium density matrix is rebuilt from the recovered
 // parameters: rho' = U diag(n_up', n_dn') U*, n_s' = (2 pi/beta)^h F_{h-1}(beta mu_s)
 // (Eq. WeqDiscr), i.e. n' = n_up' + n_dn', S' = (n_up' - n_dn') axis; u and

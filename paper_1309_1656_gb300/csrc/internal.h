@@ -61,6 +61,8 @@ struct qlbm_ctx {
     cudaGraphExec_t graph = nullptr;
     int use_graph = 1;
     int eq_path = 0;                    // QLBM_EQ_DIRECT or QLBM_EQ_FD_PARAMS
+    int mag = 0;                        // magnetic-field term enabled
+    double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};   // its per-step spin rotation
     unsigned long long *fd_fail = nullptr;   // device counter of unresolved sites
     size_t state_bytes() const { return (size_t)b * 4 * (size_t)g.P * elem_bytes; }
     size_t lam_bytes() const { return (size_t)b * 4 * (size_t)g.P * (prec == QLBM_FP64 ? 8 : 4); }
@@ -88,6 +90,8 @@ struct LatticeOps {
     cudaError_t (*step_fd)(qlbm_ctx *h, bool odd);
     cudaError_t (*fd_params_adjoint)(qlbm_ctx *h, const double *gbeta, const double *gmu_up,
                                      const double *gmu_dn, const double *gaxis, double *lam);
+    cudaError_t (*init_fd)(qlbm_ctx *h, const double *beta, const double *mu_up, const double *mu_dn,
+                           const double *axis, const double *u);
 };
 
 const LatticeOps *lattice_ops_d2q9(int prec);

@@ -82,7 +82,7 @@ __device__ __forceinline__ void gather(const Planes<typename Codec::S, Lattice<D
 
 // One AA step (even: ODD = false, odd: ODD = true), fused
 // moments + equilibrium + collision + streaming.
-template <int D, class Codec, bool ODD>
+template <int D, class Codec, bool ODD, bool MAG = false>
 __global__ void __launch_bounds__(kStepBlock, Codec::MIN_BLOCKS)
 k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typename Codec::R> k,
           Codec codec, unsigned *__restrict__ flags)
@@ -98,6 +98,7 @@ k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typena
         flag = collide_dev<D>(f, sx, sy, sz, k);
     else
         flag = collide<D, R>(f, sx, sy, sz, k);
+    if constexpr (MAG) rotate_spins<D, R>(sx, sy, sz, k.rot);
     // g.zero is 0 at run time; adding it keeps the compiler from carrying the
     // 4b load addresses (identical to the store addresses) through the
     // collision in registers.

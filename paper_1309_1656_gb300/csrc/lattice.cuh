@@ -54,7 +54,26 @@ template <typename R> struct Coll {
     R w[3];         // weights for |i|^2 = 0, 1, 2
     R g00, g01, g11, gj;
     R S2;           // sum_i w_i |i|^2 (= c / K)
+    R rot[9];       // spin rotation of the magnetic-field term (row-major), if enabled
 };
+
+// Magnetic-field term (Sec. 5): the Vlasov commutator -i[mu sigma.B, W]
+// integrated exactly over one time step is W -> U W U*,
+// U = exp(-i mu dt sigma.B), i.e. every Bloch vector s_i is rotated by
+// 2 mu |B| dt about B (ds/dt = 2 mu B x s).  It commutes with the
+// SU(2)-covariant collision, so applying it after the BGK update is exact.
+template <int D, typename R>
+__device__ __forceinline__ void rotate_spins(R *sx, R *sy, R *sz, const R (&rot)[9])
+{
+    constexpr int Q = Lattice<D>::Q;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const R x = sx[q], y = sy[q], z = sz[q];
+        sx[q] = rot[0] * x + rot[1] * y + rot[2] * z;
+        sy[q] = rot[3] * x + rot[4] * y + rot[5] * z;
+        sz[q] = rot[6] * x + rot[7] * y + rot[8] * z;
+    }
+}
 // Bits of the device flag word.
 enum : unsigned { FLAG_NONFINITE = 1u, FLAG_NONPOSITIVE = 2u };
 

@@ -36,6 +36,7 @@ template <typename R> Coll<R> make_coll(const qlbm_ctx *h)
     const double sx2 = 2.0 * k.w[1] + ((d == 2) ? 4.0 : 8.0) * k.w[2];
     c.gj = (R)(1.0 / sx2);
     c.S2 = (R)S2;
+    for (int i = 0; i < 9; ++i) c.rot[i] = (R)h->rot[i];
     return c;
 }
 
@@ -93,10 +94,17 @@ template <int D, class Codec> struct Launchers {
         const Planes<S, Q> pl = planes(h);
         const Coll<R> k = make_coll<R>(h);
         const Codec codec = make_codec<Codec>(h);
-        if (odd)
-            k_step_aa<D, Codec, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-        else
-            k_step_aa<D, Codec, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+        if (h->mag) {
+            if (odd)
+                k_step_aa<D, Codec, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+            else
+                k_step_aa<D, Codec, false, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+        } else {
+            if (odd)
+                k_step_aa<D, Codec, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+            else
+                k_step_aa<D, Codec, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+        }
         return cudaGetLastError();
     }
 
@@ -154,17 +162,27 @@ template <int D, class Codec> struct Launchers {
     static cudaError_t adjoint(qlbm_ctx *h, const void *state, const void *lam_in, void *lam_out)
     {
         const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
-        k_adjoint<D, Codec><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, state), planes_of<R>(h, lam_in),
-                                                        planes_of<R>(h, lam_out), h->g, make_coll<R>(h),
-                                                        make_codec<Codec>(h), h->dtau_acc);
+        if (h->mag)
+            k_adjoint<D, Codec, true><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, state), planes_of<R>(h, lam_in),
+                                                                  planes_of<R>(h, lam_out), h->g, make_coll<R>(h),
+                                                                  make_codec<Codec>(h), h->dtau_acc);
+        else
+            k_adjoint<D, Codec, false><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, state), planes_of<R>(h, lam_in),
+                                                                   planes_of<R>(h, lam_out), h->g, make_coll<R>(h),
+                                                                   make_codec<Codec>(h), h->dtau_acc);
         return cudaGetLastError();
     }
 
     static cudaError_t push(qlbm_ctx *h, const void *src, void *dst)
     {
         const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
-        k_step_push<D, Codec><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, src), planes_of<S>(h, dst), h->g,
-                                                          make_coll<R>(h), make_codec<Codec>(h), h->flags);
+        if (h->mag)
+            k_step_push<D, Codec, true><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, src), planes_of<S>(h, dst), h->g,
+                                                                    make_coll<R>(h), make_codec<Codec>(h), h->flags);
+        else
+            k_step_push<D, Codec, false><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, src), planes_of<S>(h, dst),
+                                                                     h->g, make_coll<R>(h), make_codec<Codec>(h),
+                                                                     h->flags);
         return cudaGetLastError();
     }
 
@@ -244,13 +262,22 @@ template <int D, class Codec> struct Launchers {
         return cudaGetLastError();
     }
 
+    static cudaError_t init_fd(qlbm_ctx *h, const double *beta, const double *mu_up, const double *mu_dn,
+                               const double *axis, const double *u)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        k_init_fd<D, Codec><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_init(h), make_codec<Codec>(h), beta,
+                                                        mu_up, mu_dn, axis, u);
+        return cudaGetLastError();
+    }
+
     static const LatticeOps *table()
     {
         static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
                                      &conserved_partial, &adjoint, &push, &copy_natural, &lam_import,
                                      &lam_export, &init_adjoint, &fd_params,
                                      std::is_same<Codec, CodecF64>::value ? &step_fd : nullptr,
-                                     &fd_params_adjoint};
+                                     &fd_params_adjoint, &init_fd};
         return &t;
     }
 };

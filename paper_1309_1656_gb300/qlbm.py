@@ -73,6 +73,8 @@ _rollout_adjoint = _sig("qlbm_rollout_adjoint", _i, [_vp, _vp, _vp, ctypes.POINT
 _init_adjoint = _sig("qlbm_init_equilibrium_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i])
 _fd_params = _sig("qlbm_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64), _i])
 _fd_params_adjoint = _sig("qlbm_fd_params_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
+_init_fd = _sig("qlbm_init_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
+_set_field = _sig("qlbm_set_magnetic_field", _i, [_vp, _d, ctypes.POINTER(_d)])
 _set_eq_path = _sig("qlbm_set_equilibrium_path", _i, [_vp, _i])
 _conserved_static = _sig("qlbm_conserved_static", _i, [_i, ctypes.POINTER(_i64), _d, _vp, _vp, _vp])
 
@@ -221,6 +223,16 @@ def qlbm_fd_params_adjoint(h, lam, g_beta=None, g_mu_up=None, g_mu_dn=None, g_ax
     _check(_fd_params_adjoint(h, *[x[0] for x in p], _kind(*p)), h)
 
 
+def qlbm_init_fd_params(h, beta, mu_up, mu_dn, axis, u):
+    p = [_ptr(beta), _ptr(mu_up), _ptr(mu_dn), _ptr(axis), _ptr(u)]
+    _check(_init_fd(h, *[x[0] for x in p], _kind(*p)), h)
+
+
+def qlbm_set_magnetic_field(h, mu, B):
+    b = (ctypes.c_double * 3)(*[float(v) for v in B])
+    _check(_set_field(h, float(mu), b), h)
+
+
 def qlbm_set_equilibrium_path(h, path):
     _check(_set_eq_path(h, int(path)), h)
 
@@ -321,6 +333,9 @@ class Lattice:
         axis = np.zeros((3, self.N))
         nfail = qlbm_fd_params(self.h, beta, mu_up, mu_dn, axis)
         return beta, mu_up, mu_dn, axis, nfail
+
+    def set_magnetic_field(self, mu, B):
+        qlbm_set_magnetic_field(self.h, mu, B)
 
     def set_equilibrium_path(self, path):
         qlbm_set_equilibrium_path(self.h, path)

@@ -136,3 +136,27 @@ def test_fd_params_adjoint_vs_finite_differences(q, d, dims):
             fd = (J(W + h * dv) - J(W - h * dv)) / (2 * h)
             ad = float(np.sum(lam * dv))
             assert ad == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+@pytest.mark.parametrize("d,dims", [(2, (11, 6, 1)), (3, (5, 4, 3))])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-7)])
+def test_init_from_fd_parameters(q, oracle_mod, d, dims, prec, tol):
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(d + 30)
+    beta = rng.uniform(0.5, 2.0, N)
+    mu_up = rng.uniform(-3.0, 1.0, N)
+    mu_dn = mu_up - rng.uniform(0.0, 1.0, N)
+    axis = rng.normal(size=(3, N))
+    axis /= np.linalg.norm(axis, axis=0)
+    u = rng.uniform(-0.1, 0.1, (d, N))
+    rho4 = np.zeros((4, N))
+    eps = np.zeros(N)
+    for s in range(N):
+        nu, nd, e = oracle_mod.fd_moments(d, beta[s], mu_up[s], mu_dn[s])
+        rho4[:, s] = np.r_[nu + nd, (nu - nd) * axis[:, s]]
+        eps[s] = e
+    ref = oracle_mod.init_equilibrium(d, dims, 1.0, rho4, u, eps)
+    with q.Lattice(d, dims, 0.8, 1.0, precision=prec) as lat:
+        q.qlbm_init_fd_params(lat.h, beta, mu_up, mu_dn, axis, u)
+        got = lat.get_state()
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < tol
