@@ -476,13 +476,14 @@ def cpu_baseline(w, target_s=15.0):
     cores = oracle.max_threads(0)
     st = oracle.init_equilibrium(d, dims, w["beta0"], fl["rho4"], fl["u"], fl["eps"])
     st = oracle.run(d, dims, w["tau"], w["beta0"], 2, st)      # thread start-up
-    t = time.perf_counter()
-    st = oracle.run(d, dims, w["tau"], w["beta0"], 3, st)
-    t1 = (time.perf_counter() - t) / 3.0
-    n = int(max(1, min(20000, target_s / max(t1, 1e-6))))
-    t = time.perf_counter()
-    oracle.run(d, dims, w["tau"], w["beta0"], n, st)
-    dt = time.perf_counter() - t
+    # run in chunks until the sample has taken target_s of wall time
+    n, chunk, dt = 0, 8, 0.0
+    while dt < target_s:
+        t = time.perf_counter()
+        st = oracle.run(d, dims, w["tau"], w["beta0"], chunk, st)
+        dt += time.perf_counter() - t
+        n += chunk
+        chunk = min(2 * chunk, 4096)
     return {"value": round(N * n / dt / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": "%s sub-lattice %s of the same workload recipe, %d FP64 steps, %.1f s" %
                       ("D3Q19" if d == 3 else "D2Q9", "x".join(map(str, dims)), n, dt)}

@@ -215,6 +215,22 @@ def shear2d(nx=4096, ny=4096, seed=3, U0=0.04, delta=80.0, noise=1e-3, spin=0.1)
     return dict(rho4=rho4, u=u, eps=None)
 
 
+def dichotomic3d(L=32, spin=0.1, umax=0.05, sharp=4.0):
+    """Uniform density, Bloch vectors along z with a dichotomic outline
+    r_z = spin tanh(sharp sin(2 pi x/L) sin(2 pi y/L)) and a velocity along x
+    proportional to r_z (|u_x| <= umax): the shape of the paper's 3D
+    convergence example (its exact outline is not given)."""
+    x, y, _ = _coords((L, L, L))
+    prof = np.tanh(sharp * np.sin(2 * np.pi * x / L) * np.sin(2 * np.pi * y / L))
+    N = L ** 3
+    rho4 = np.zeros((4, N))
+    rho4[0] = 1.0
+    rho4[3] = spin * prof
+    u = np.zeros((3, N))
+    u[0] = umax * prof
+    return dict(rho4=rho4, u=u, eps=None)
+
+
 def random_fields(d, dims, seed=4, umax=0.2, eps_range=(0.8, 2.2), spin_frac=0.6):
     """Random per-site (rho, u, eps): n in [0.5, 1.5], |S| < spin_frac * n."""
     dims = _dims3(d, dims)
