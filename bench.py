@@ -321,7 +321,7 @@ def bench_ours(args):
         fdp = {"fd_params_ms": round(t_fd, 3), "fd_params_msites_per_s": round(N / t_fd / 1e3, 1),
                "fd_path_step_ms": round(t_step, 3), "fd_path_mlups": round(N / t_step / 1e3, 1),
                "unresolved_sites": nfail, "beta_median": float(outs[0].median()),
-               "note": "FP64 per-site eigen-decomposition + nested Newton (Prop. 1); cost reported "
+               "note": "FP64 per-site eigen-decomposition + Newton on the 3x3 logarithmic system (Prop. 1); cost reported "
                        "separately, the paper's step does not need it"}
         lat.close()
         del outs, ax

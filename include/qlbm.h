@@ -175,8 +175,11 @@ int qlbm_set_magnetic_field(qlbm_handle h, double mu, const double B[3]);
  * (beta, mu_up, mu_dn) then solve Eqs. nFDstdOmega and energyFDstdOmega,
  *   n_s = (2 pi/beta)^(d/2) F_{d/2-1}(beta mu_s),
  *   tr(rho) eps = (d/2) beta^-1 (2 pi/beta)^(d/2) sum_s F_{d/2}(beta mu_s),
- * by a Newton iteration per eigenvalue nested in a bracketed Newton iteration
- * on log beta, in double precision whatever the storage precision.
+ * by Newton's method on the logarithms of the three equations in
+ * (log beta, beta mu_up, beta mu_dn) from the classical limit (a site where it
+ * does not settle is solved again by a per-eigenvalue Newton inversion nested
+ * in a bracketed Newton iteration on log beta), in double precision whatever
+ * the storage precision.
  *   beta, mu_up, mu_dn  [N] (any may be NULL);  axis [3][N] (or NULL), zero
  *   where |S| = 0 (U arbitrary).  Sites where rho is not positive definite
  *   or no beta fits (eps below the zero-temperature limit) get NaN and are

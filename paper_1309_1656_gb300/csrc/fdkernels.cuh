@@ -95,11 +95,11 @@ k_fd_params_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, C
         // cotangent of (beta, nu_up, nu_dn)
         const double pb0 = bb - (b1 * p.mu_up + b2 * p.mu_dn) / beta, pb1 = b1 / beta, pb2 = b2 / beta;
         const double A = pow(kTwoPi / beta, h);
-        const double F1 = fd_hm1<D>(nu1), F2 = fd_hm1<D>(nu2);
-        const double Fh = fd_h<D>(nu1) + fd_h<D>(nu2);
+        const Fd3 G1 = fd3<D>(nu1), G2 = fd3<D>(nu2);
+        const double F1 = G1.m1, F2 = G2.m1, Fh = G1.h + G2.h;
         // J rows: G1, G2, G3; columns: beta, nu_up, nu_dn
-        const double J00 = -h / beta * A * F1, J01 = A * fd_hm2<D>(nu1);
-        const double J10 = -h / beta * A * F2, J12 = A * fd_hm2<D>(nu2);
+        const double J00 = -h / beta * A * F1, J01 = A * G1.m2;
+        const double J10 = -h / beta * A * F2, J12 = A * G2.m2;
         const double J20 = -(h + 1.0) / beta * h / beta * A * Fh, J21 = h / beta * A * F1, J22 = h / beta * A * F2;
         // solve J^T mbar = pbar:
         //   J00 m0 + J10 m1 + J20 m2 = pb0
@@ -161,10 +161,11 @@ k_init_fd(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, InitConsts 
     const int64_t N = g.N, s = si.s;
     const double b = beta[s], nu1 = b * mu_up[s], nu2 = b * mu_dn[s];
     const double pre = pow(kTwoPi / b, h);
-    const double F1 = fd_hm1<D>(nu1), F2 = fd_hm1<D>(nu2);
+    const Fd3 G1 = fd3<D>(nu1), G2 = fd3<D>(nu2);
+    const double F1 = G1.m1, F2 = G2.m1;
     const double nup = pre * F1, ndn = pre * F2;
     const double n = nup + ndn;
-    const double e = h / b * (fd_h<D>(nu1) + fd_h<D>(nu2)) / (F1 + F2);
+    const double e = h / b * (G1.h + G2.h) / (F1 + F2);
     const double Sx = (nup - ndn) * axis[s], Sy = (nup - ndn) * axis[N + s], Sz = (nup - ndn) * axis[2 * N + s];
     const double jx = u[s] / ic.xi, jy = u[N + s] / ic.xi, jz = (D == 3) ? u[2 * N + s] / ic.xi : 0.0;
     const double be = ic.beta0 * e;
@@ -189,7 +190,6 @@ __device__ __forceinline__ unsigned collide_fd(double *f, double *sx, double *sy
                                                const Coll<double> &k, const FdArgs &a)
 {
     constexpr int Q = Lattice<D>::Q;
-    constexpr double h = 0.5 * D;
     SiteMoments<D, double> m = site_moments<D, double>(f, sx, sy, sz);
     const double jj = m.jx * m.jx + m.jy * m.jy + m.jz * m.jz;
     const double be = k.K * (m.e2n - jj);   // beta0 * eps
@@ -197,8 +197,7 @@ __device__ __forceinline__ unsigned collide_fd(double *f, double *sx, double *sy
     unsigned flag = 0u;
     const FdParams p = fd_params_site<D>(m.n, m.Sx, m.Sy, m.Sz, be / a.beta0);
     if (p.status == 0) {
-        const double pre = pow(kTwoPi / p.beta, h);
-        const double nu = pre * fd_hm1<D>(p.beta * p.mu_up), nd = pre * fd_hm1<D>(p.beta * p.mu_dn);
+        const double nu = p.n_up, nd = p.n_dn;
         n2 = nu + nd;
         Sx2 = (nu - nd) * p.ax;
         Sy2 = (nu - nd) * p.ay;

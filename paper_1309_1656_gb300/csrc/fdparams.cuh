@@ -8,11 +8,16 @@
 // be recovered by diagonalizing rho"); then (beta, nu_up, nu_dn), nu = beta mu,
 // solve
 //   n_s = (2 pi/beta)^h F_{h-1}(nu_s),   n eps = h beta^-1 (2 pi/beta)^h sum_s F_h(nu_s),
-// h = d/2.  For a trial beta each species is inverted on its own (closed form
-// in 2D, F_0(nu) = log(1 + e^nu); Newton on log F_{1/2} in 3D), and beta is
-// found by a bracketed Newton iteration on log beta of the energy equation,
-// using d nu_s / d beta = h F_{h-1}(nu_s) / (beta F_{h-2}(nu_s)) (from
-// dF_k/dx = F_{k-1}).
+// h = d/2.  The three equations are solved together by Newton's method on
+// their logarithms in the unknowns (log beta, nu_up, nu_dn), started from the
+// classical limit F_k(x) ~ e^x (where the logarithmic system is linear), with
+// the Jacobian from dF_k/dx = F_{k-1}; each iteration evaluates F_{h-2},
+// F_{h-1}, F_h of both species in one pass.  A site on which that iteration
+// does not settle is solved again by the nested method: for a trial beta each
+// species is inverted on its own (closed form in 2D, F_0(nu) = log(1 + e^nu);
+// Newton on log F_{1/2} in 3D), and beta is found by a bracketed Newton
+// iteration on log beta of the energy equation, using
+// d nu_s / d beta = h F_{h-1}(nu_s) / (beta F_{h-2}(nu_s)).
 #pragma once
 
 #include <math_constants.h>
@@ -109,15 +114,121 @@ template <int D> __device__ __forceinline__ double species_nu(double beta, doubl
 
 struct FdParams {
     double beta, mu_up, mu_dn, ax, ay, az;
-    int status;   // 0 ok, 1 rho not positive definite, 2 no beta fits / no convergence
+    double n_up, n_dn;   // (2 pi/beta)^h F_{h-1}(beta mu_s) at the solution
+    int status;          // 0 ok, 1 rho not positive definite, 2 no beta fits / no convergence
 };
 
+// Alternating series sum_{n>=1} (-1)^(n+1) q^n / n^(k+1), q = e^x <= 1/e, for
+// the NK tables from K0, truncated after NT terms: the series alternates with
+// decreasing terms, so the error is below q^(NT+1), and F_k >= q/2.
+template <int NT, int K0, int NK>
+__device__ __forceinline__ void fd_series_nt(double q, double *out)
+{
+    double acc[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int n = NT - 1; n >= 0; --n) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            acc[k] = fma(q, acc[k], (n & 1) ? -FD_SERIES[K0 + k][n] : FD_SERIES[K0 + k][n]);
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) out[k] = q * acc[k];
+}
+
+// The same at q = e^x, x <= -1, with as many terms as keep 2 q^NT below
+// 1e-17 relative: 6 for x <= -8, 14 for x <= -3, else the full table.
+template <int K0, int NK>
+__device__ __forceinline__ void fd_series(double x, double q, double *out)
+{
+    if (x <= -8.0) fd_series_nt<6, K0, NK>(q, out);
+    else if (x <= -3.0) fd_series_nt<14, K0, NK>(q, out);
+    else fd_series_nt<FD_NSER, K0, NK>(q, out);
+}
+
+// F_{h-2}, F_{h-1}, F_h (h = D/2) at one argument, sharing the exponential,
+// the interval and the powers between the three.
+struct Fd3 {
+    double m2, m1, h;
+};
+
+template <int D> __device__ __forceinline__ Fd3 fd3(double x)
+{
+    Fd3 r;
+    if (D == 2) {   // F_-1 = (1 + e^-x)^-1, F_0 = log(1 + e^x), F_1 (tables)
+        double o[1];
+        if (x <= -1.0) {
+            const double q = exp(x);
+            r.m2 = q / (1.0 + q);
+            r.m1 = log1p(q);
+            fd_series<3, 1>(x, q, o);
+            r.h = o[0];
+        } else if (x < 1.0) {
+            const double e = exp(x);
+            r.m2 = e / (1.0 + e);
+            r.m1 = log1p(e);
+            double acc = 0.0;
+            for (int j = FD_NTAY - 1; j >= 0; --j) acc = fma(x, acc, FD_TAYLOR[3][j]);
+            r.h = acc;
+        } else {        // F_1(x) = x^2/2 + pi^2/6 - F_1(-x)
+            const double q = exp(-x);
+            r.m2 = 1.0 / (1.0 + q);
+            r.m1 = x + log1p(q);
+            fd_series<3, 1>(-x, q, o);
+            r.h = 0.5 * x * x + 1.6449340668482264 - o[0];
+        }
+        return r;
+    }
+    double o[3];
+    if (x <= -1.0) {
+        fd_series<0, 3>(x, exp(x), o);
+    } else if (x < 1.0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double acc = 0.0;
+            for (int j = FD_NTAY - 1; j >= 0; --j) acc = fma(x, acc, FD_TAYLOR[k][j]);
+            o[k] = acc;
+        }
+    } else if (x < FD_X0 + FD_NINT * FD_WIDTH) {
+        const int i = (int)((x - FD_X0) / FD_WIDTH);
+        const double a = FD_X0 + FD_WIDTH * i;
+        const double t = (x - a - 0.5 * FD_WIDTH) / (0.5 * FD_WIDTH);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double *c = FD_CHEB[k][i];
+            double b1 = 0.0, b2 = 0.0;
+            for (int j = FD_NCHEB - 1; j >= 1; --j) {
+                const double b0 = fma(2.0 * t, b1, c[j] - b2);
+                b2 = b1;
+                b1 = b0;
+            }
+            o[k] = fma(t, b1, c[0] - b2);
+        }
+    } else {        // Sommerfeld: x^(k+1)/Gamma(k+2) (1 + sum_n a_n x^-2n), k + 1 = 1/2, 3/2, 5/2
+        const double r2 = 1.0 / (x * x), sq = sqrt(x);
+        const double xp[3] = {sq, x * sq, x * x * sq};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double acc = 0.0;
+            for (int n = FD_NASYM - 1; n >= 1; --n) acc = fma(r2, acc, FD_ASYM[k][n]);
+            o[k] = xp[k] * FD_ASYM[k][0] * fma(r2, acc, 1.0);
+        }
+    }
+    r.m2 = o[0];
+    r.m1 = o[1];
+    r.h = o[2];
+    return r;
+}
+
+// The nested solve (bracketed Newton on log beta around the per-species
+// inversion); the fallback of fd_params_site.
 template <int D>
-__device__ FdParams fd_params_site(double n, double Sx, double Sy, double Sz, double eps)
+__device__ FdParams fd_params_nested(double n, double Sx, double Sy, double Sz, double eps)
 {
     constexpr double h = 0.5 * D;
     FdParams p;
-    p.beta = p.mu_up = p.mu_dn = p.ax = p.ay = p.az = CUDART_NAN;
+    p.beta = p.mu_up = p.mu_dn = p.ax = p.ay = p.az = p.n_up = p.n_dn = CUDART_NAN;
     const double nS = sqrt(Sx * Sx + Sy * Sy + Sz * Sz);
     const double nup = 0.5 * (n + nS), ndn = 0.5 * (n - nS);
     if (!(ndn > 0.0)) {
@@ -174,6 +285,81 @@ __device__ FdParams fd_params_site(double n, double Sx, double Sy, double Sz, do
     nu2 = nS > 0.0 ? species_nu<D>(p.beta, ndn) : nu1;
     p.mu_up = nu1 / p.beta;
     p.mu_dn = nu2 / p.beta;
+    const double A = pow(kTwoPi / p.beta, h);
+    p.n_up = A * fd_hm1<D>(nu1);
+    p.n_dn = nS > 0.0 ? A * fd_hm1<D>(nu2) : p.n_up;
+    p.status = 0;
+    return p;
+}
+
+// Newton's method on
+//   r_1 = log F_{h-1}(nu_up) - h t + h log 2 pi - log n_up
+//   r_2 = log F_{h-1}(nu_dn) - h t + h log 2 pi - log n_dn
+//   r_3 = log(F_h(nu_up) + F_h(nu_dn)) - (h+1) t + h log 2 pi - log(n eps / h),
+// t = log beta.  With g_s = F_{h-2}/F_{h-1}(nu_s) and c_s = F_{h-1}(nu_s)/sum F_h
+// the Jacobian is [[-h, g_up, 0], [-h, 0, g_dn], [-(h+1), c_up, c_dn]]; its
+// Schur complement -(h+1) + h sum_s c_s/g_s is negative (positive heat
+// capacity), so the step is always defined.
+template <int D>
+__device__ FdParams fd_params_site(double n, double Sx, double Sy, double Sz, double eps)
+{
+    constexpr double h = 0.5 * D;
+    constexpr double hl2pi = h * 1.8378770664093453;   // h log 2 pi
+    FdParams p;
+    p.beta = p.mu_up = p.mu_dn = p.ax = p.ay = p.az = p.n_up = p.n_dn = CUDART_NAN;
+    const double nS = sqrt(Sx * Sx + Sy * Sy + Sz * Sz);
+    const double nup = 0.5 * (n + nS), ndn = 0.5 * (n - nS);
+    if (!(ndn > 0.0)) {
+        p.status = 1;
+        return p;
+    }
+    if (nS > 0.0) {
+        p.ax = Sx / nS;
+        p.ay = Sy / nS;
+        p.az = Sz / nS;
+    } else {
+        p.ax = p.ay = p.az = 0.0;
+    }
+    if (!(eps > 0.0)) {
+        p.status = 2;
+        return p;
+    }
+    const bool split = nS > 0.0;
+    const double lA = log(nup), lB = split ? log(ndn) : lA, lC = log(n * eps / h);
+    double t = log(h / eps);
+    double nu1 = lA - hl2pi + h * t, nu2 = lB - hl2pi + h * t;
+    Fd3 F1, F2;
+    bool settled = false;
+    for (int it = 0;; ++it) {
+        F1 = fd3<D>(nu1);
+        F2 = split ? fd3<D>(nu2) : F1;
+        if (settled || it == 40) break;
+        const double sFh = F1.h + F2.h;
+        const double r1 = log(F1.m1) - h * t + hl2pi - lA;
+        const double r2 = split ? log(F2.m1) - h * t + hl2pi - lB : r1;
+        const double r3 = log(sFh) - (h + 1.0) * t + hl2pi - lC;
+        const double ig1 = F1.m1 / F1.m2, ig2 = F2.m1 / F2.m2;   // 1/g_s
+        const double c1 = F1.m1 / sFh, c2 = F2.m1 / sFh;
+        const double den = -(h + 1.0) + h * (c1 * ig1 + c2 * ig2);
+        double dt = (c1 * ig1 * r1 + c2 * ig2 * r2 - r3) / den;
+        if (!(dt == dt)) break;
+        dt = fmax(-1.0, fmin(1.0, dt));
+        const double d1 = fmax(-10.0, fmin(10.0, (h * dt - r1) * ig1));
+        const double d2 = fmax(-10.0, fmin(10.0, (h * dt - r2) * ig2));
+        t += dt;
+        nu1 += d1;
+        nu2 = split ? nu2 + d2 : nu1;
+        // quadratic convergence: once a step is below 1e-9 the iterate is exact
+        // to rounding; one more evaluation gives the outputs at it
+        settled = fmax(fabs(dt), fmax(fabs(d1), fabs(d2))) <= 1e-9;
+    }
+    if (!settled) return fd_params_nested<D>(n, Sx, Sy, Sz, eps);
+    const double A = exp(hl2pi - h * t);
+    p.beta = exp(t);
+    p.mu_up = nu1 / p.beta;
+    p.mu_dn = nu2 / p.beta;
+    p.n_up = A * F1.m1;
+    p.n_dn = A * F2.m1;
     p.status = 0;
     return p;
 }

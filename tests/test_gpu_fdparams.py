@@ -70,6 +70,51 @@ def test_fd_params_round_trip(q, oracle_mod, d):
     assert np.all(ax[:, :2] == 0.0)
 
 
+REGIMES = {   # nu_up = beta mu_up range, nu_up - nu_dn range
+    "classical": ((-30.0, -8.0), (0.0, 5.0)),
+    "intermediate": ((-8.0, 1.0), (0.0, 5.0)),
+    "degenerate": ((1.0, 40.0), (0.0, 5.0)),
+    # n_dn / n_up down to ~1e-4: n_dn = (n - |S|)/2 keeps ~12 digits
+    "polarised": ((0.0, 10.0), (6.0, 9.0)),
+}
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("regime", sorted(REGIMES))
+def test_fd_params_round_trip_regimes(q, oracle_mod, d, regime):
+    # every branch of the device F_k evaluation (series lengths, Taylor,
+    # Chebyshev, Sommerfeld) and the Newton solve far from its classical
+    # starting point
+    dims = (5, 4, 1) if d == 2 else (3, 3, 2)
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(d + 31 + len(regime))
+    (a1, b1), (g1, g2) = REGIMES[regime]
+    beta = rng.uniform(0.3, 3.0, N)
+    nu_up = rng.uniform(a1, b1, N)
+    nu_dn = nu_up - rng.uniform(g1, g2, N)
+    axis = rng.normal(size=(3, N))
+    axis /= np.linalg.norm(axis, axis=0)
+    rho4 = np.zeros((4, N))
+    eps = np.zeros(N)
+    for s in range(N):
+        nu, nd, e = oracle_mod.fd_moments(d, beta[s], nu_up[s] / beta[s], nu_dn[s] / beta[s])
+        rho4[0, s] = nu + nd
+        rho4[1:, s] = (nu - nd) * axis[:, s]
+        eps[s] = e
+    with q.Lattice(d, dims, 0.8, 1.0) as lat:
+        lat.init_equilibrium(rho4, np.zeros((d, N)), eps)
+        b, mu, md, ax, nfail = lat.fd_params()
+    assert nfail == 0
+    # beta is ill-conditioned in the degenerate limit (eps depends on it only
+    # at order (pi/nu)^2): relative error ~ 1e-16 nu^2
+    tol_b = 1e-10 if regime != "degenerate" else 1e-8
+    assert np.allclose(b, beta, rtol=tol_b)
+    assert np.allclose(mu * b, nu_up, rtol=1e-9, atol=1e-9)
+    assert np.allclose(md * b, nu_dn, rtol=1e-9, atol=1e-9)
+    moved = nu_up != nu_dn
+    assert np.allclose(ax[:, moved], axis[:, moved], atol=1e-9)
+
+
 def test_fd_params_invalid_sites(q):
     d, dims = 3, (4, 2, 2)
     N = 16
