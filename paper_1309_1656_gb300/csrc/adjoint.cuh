@@ -153,12 +153,11 @@ __device__ __forceinline__ void adj_accumulate(const Planes<typename Codec::S, L
                                                MuMom<typename Codec::R> &Bz)
 {
     using R = typename Codec::R;
-    const R f = codec.load(st.p[4 * q][si.s]);
-    const R sx = codec.load(st.p[4 * q + 1][si.s]);
-    const R sy = codec.load(st.p[4 * q + 2][si.s]);
-    const R sz = codec.load(st.p[4 * q + 3][si.s]);
+    R f, sx, sy, sz;
+    codec.load4(st.p[q] + si.s, f, sx, sy, sz);
     const int s = neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q));
-    R mf = lin.p[4 * q][s], mx = lin.p[4 * q + 1][s], my = lin.p[4 * q + 2][s], mz = lin.p[4 * q + 3][s];
+    R mf, mx, my, mz;
+    ldq(lin.p[q] + s, mf, mx, my, mz);
     if constexpr (MAG) unrotate(mx, my, mz, k.rot);
     fw[0] += f;
     fw[1] += sx;
@@ -295,14 +294,12 @@ k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typena
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int s = neighbour(g, s2, cx<D>(q), cy<D>(q), cz<D>(q));
-            R mf = lin.p[4 * q][s], mx = lin.p[4 * q + 1][s], my = lin.p[4 * q + 2][s],
-              mz = lin.p[4 * q + 3][s];
+            R mf, mx, my, mz;
+            ldq(lin.p[q] + s, mf, mx, my, mz);
             if constexpr (MAG) unrotate(mx, my, mz, k.rot);
-            lout.p[4 * q][s2.s] = omc * mf + nbar +
-                                  (cx<D>(q) * Jbx2 + cy<D>(q) * Jby2 + cz<D>(q) * Jbz2) + cnorm2<D>(q) * Eb;
-            lout.p[4 * q + 1][s2.s] = omc * mx + Sbx;
-            lout.p[4 * q + 2][s2.s] = omc * my + Sby;
-            lout.p[4 * q + 3][s2.s] = omc * mz + Sbz;
+            stq(lout.p[q] + s2.s,
+                omc * mf + nbar + (cx<D>(q) * Jbx2 + cy<D>(q) * Jby2 + cz<D>(q) * Jbz2) + cnorm2<D>(q) * Eb,
+                omc * mx + Sbx, omc * my + Sby, omc * mz + Sbz);
         }
     }
     const double bs = block_sum_double<R>(dtau);
@@ -331,10 +328,7 @@ k_step_push(const Planes<typename Codec::S, Lattice<D>::Q> src, const Planes<typ
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int s = neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q));
-        dst.p[4 * q][s] = codec.store(f[q]);
-        dst.p[4 * q + 1][s] = codec.store(sx[q]);
-        dst.p[4 * q + 2][s] = codec.store(sy[q]);
-        dst.p[4 * q + 3][s] = codec.store(sz[q]);
+        codec.store4(dst.p[q] + s, f[q], sx[q], sy[q], sz[q]);
     }
     if (flag) atomicOr(flags, flag);
 }
@@ -352,12 +346,7 @@ k_copy_natural(const Planes<typename Codec::S, Lattice<D>::Q> src, const Planes<
     R f[Q], sx[Q], sy[Q], sz[Q];
     gather<D, Codec, SWAPPED>(src, g, si, codec, f, sx, sy, sz);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        dst.p[4 * q][si.s] = codec.store(f[q]);
-        dst.p[4 * q + 1][si.s] = codec.store(sx[q]);
-        dst.p[4 * q + 2][si.s] = codec.store(sy[q]);
-        dst.p[4 * q + 3][si.s] = codec.store(sz[q]);
-    }
+    for (int q = 0; q < Q; ++q) codec.store4(dst.p[q] + si.s, f[q], sx[q], sy[q], sz[q]);
 }
 
 // Cotangent conversion between the canonical double layout [b][4][N] and the
@@ -369,8 +358,12 @@ k_lam_import(const double *__restrict__ in, const Planes<R, Lattice<D>::Q> lam, 
     constexpr int Q = Lattice<D>::Q;
     SiteIdx si;
     if (!site_of_block(g, si)) return;
+    const int64_t N = g.N;
 #pragma unroll
-    for (int k = 0; k < 4 * Q; ++k) lam.p[k][si.s] = (R)in[(int64_t)k * g.N + si.s];
+    for (int q = 0; q < Q; ++q) {
+        const double *v = in + (int64_t)(4 * q) * N + si.s;
+        stq(lam.p[q] + si.s, (R)v[0], (R)v[N], (R)v[2 * N], (R)v[3 * N]);
+    }
 }
 
 template <int D, typename R>
@@ -380,8 +373,17 @@ k_lam_export(const Planes<R, Lattice<D>::Q> lam, Grid g, double *__restrict__ ou
     constexpr int Q = Lattice<D>::Q;
     SiteIdx si;
     if (!site_of_block(g, si)) return;
+    const int64_t N = g.N;
 #pragma unroll
-    for (int k = 0; k < 4 * Q; ++k) out[(int64_t)k * g.N + si.s] = (double)lam.p[k][si.s];
+    for (int q = 0; q < Q; ++q) {
+        R a, b, c, d;
+        ldq(lam.p[q] + si.s, a, b, c, d);
+        double *o = out + (int64_t)(4 * q) * N + si.s;
+        o[0] = (double)a;
+        o[N] = (double)b;
+        o[2 * N] = (double)c;
+        o[3 * N] = (double)d;
+    }
 }
 
 // Adjoint of the equilibrium initialisation W_i = w_i P_i(u, eps) rho

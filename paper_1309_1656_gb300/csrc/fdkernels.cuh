@@ -173,10 +173,8 @@ k_init_fd(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, InitConsts 
     for (int q = 0; q < Q; ++q) {
         const int cls = cnorm2<D>(q);
         const double wp = ic.w[cls] * poly_P_d<D>(ic, q, jx, jy, jz, be);
-        pl.p[4 * q][s] = codec.from_double(wp * n, 0, cls);
-        pl.p[4 * q + 1][s] = codec.from_double(wp * Sx, 1, cls);
-        pl.p[4 * q + 2][s] = codec.from_double(wp * Sy, 2, cls);
-        pl.p[4 * q + 3][s] = codec.from_double(wp * Sz, 3, cls);
+        stq(pl.p[q] + s, codec.from_double(wp * n, 0, cls), codec.from_double(wp * Sx, 1, cls),
+            codec.from_double(wp * Sy, 2, cls), codec.from_double(wp * Sz, 3, cls));
     }
 }
 
@@ -242,10 +240,7 @@ k_step_aa_fd(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<double> k, FdA
     for (int q = 0; q < Q; ++q) {
         const int slot = ODD ? q : opposite<D>(q);
         const int s = ODD ? neighbour(g, so, cx<D>(q), cy<D>(q), cz<D>(q)) : so.s;
-        pl.p[4 * slot][s] = f[q];
-        pl.p[4 * slot + 1][s] = sx[q];
-        pl.p[4 * slot + 2][s] = sy[q];
-        pl.p[4 * slot + 3][s] = sz[q];
+        stq(pl.p[slot] + s, f[q], sx[q], sy[q], sz[q]);
     }
     if (flag) atomicOr(flags, flag);
 }

@@ -2,9 +2,10 @@
 // D = 3: D3Q19) and the storage codec.  Instantiated once per lattice in
 // kernels_d2q9.cu / kernels_d3q19.cu.
 //
-// Memory layout (HBM): one population buffer of b*4 planes, plane k = 4q + c
-// holding component c of slot q for all sites, plane stride P >= N elements
-// (padded to 64 elements), site s = x + nx*(y + ny*z).  Streaming is done in
+// Memory layout (HBM): one population buffer of b slot planes, plane q
+// holding, for every site, the vector of the four components (f, s_x, s_y,
+// s_z) of slot q; plane stride P >= N vectors (padded to 64), site
+// s = x + nx*(y + ny*z).  Streaming is done in
 // place with the AA pattern (Bailey et al., 2009):
 //   even step:  read slot q at x              -> population q at x,
 //               write population q' to slot opposite(q') at x;
@@ -26,11 +27,12 @@ namespace qlbm {
 constexpr int kStepBlock = 128;   // threads per block along x
 constexpr int kRedBlock = 256;    // threads per block of the reductions
 
-// Base pointers of the b*4 component planes, passed by value so that every
-// access is one multiply-add of a 32-bit site index onto a constant-bank
-// pointer (keeps the 4b addresses out of registers).
+// Base pointers of the b slot planes (vectors of the four components of
+// storage type S), passed by value so that every access is one multiply-add
+// of a 32-bit site index onto a constant-bank pointer (keeps the b addresses
+// out of registers).
 template <class S, int Q> struct Planes {
-    S *p[4 * Q];
+    typename QuadOf<S>::V *p[Q];
 };
 
 // Site of the calling thread; false if it lies beyond the row.
@@ -73,10 +75,7 @@ __device__ __forceinline__ void gather(const Planes<typename Codec::S, Lattice<D
     for (int q = 0; q < Q; ++q) {
         const int p = SWAPPED ? opposite<D>(q) : q;     // population held by slot q
         const int s = SWAPPED ? neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q)) : si.s;
-        f[p] = codec.load(pl.p[4 * q][s]);
-        sx[p] = codec.load(pl.p[4 * q + 1][s]);
-        sy[p] = codec.load(pl.p[4 * q + 2][s]);
-        sz[p] = codec.load(pl.p[4 * q + 3][s]);
+        codec.load4(pl.p[q] + s, f[p], sx[p], sy[p], sz[p]);
     }
 }
 
@@ -110,10 +109,7 @@ k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typena
         // population q goes to slot opposite(q) at x (even) or slot q at x + e_q (odd)
         const int slot = ODD ? q : opposite<D>(q);
         const int s = ODD ? neighbour(g, so, cx<D>(q), cy<D>(q), cz<D>(q)) : so.s;
-        pl.p[4 * slot][s] = codec.store(f[q]);
-        pl.p[4 * slot + 1][s] = codec.store(sx[q]);
-        pl.p[4 * slot + 2][s] = codec.store(sy[q]);
-        pl.p[4 * slot + 3][s] = codec.store(sz[q]);
+        codec.store4(pl.p[slot] + s, f[q], sx[q], sy[q], sz[q]);
     }
     if (flag) atomicOr(flags, flag);
 }
@@ -155,10 +151,8 @@ k_init_eq(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, InitConsts 
     for (int q = 0; q < Q; ++q) {
         const int cls = cnorm2<D>(q);
         const double wp = ic.w[cls] * poly_P_d<D>(ic, q, jx, jy, jz, be);
-        pl.p[4 * q][s] = codec.from_double(wp * n, 0, cls);
-        pl.p[4 * q + 1][s] = codec.from_double(wp * Sx, 1, cls);
-        pl.p[4 * q + 2][s] = codec.from_double(wp * Sy, 2, cls);
-        pl.p[4 * q + 3][s] = codec.from_double(wp * Sz, 3, cls);
+        stq(pl.p[q] + s, codec.from_double(wp * n, 0, cls), codec.from_double(wp * Sx, 1, cls),
+            codec.from_double(wp * Sy, 2, cls), codec.from_double(wp * Sz, 3, cls));
     }
 }
 
@@ -199,8 +193,8 @@ k_set_state(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec cod
     for (int q = 0; q < Q; ++q) {
         const double *v = in + (int64_t)(4 * q) * N + si.s;
         const int cls = cnorm2<D>(q);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) pl.p[4 * q + c][si.s] = codec.from_double(v[c * N], c, cls);
+        stq(pl.p[q] + si.s, codec.from_double(v[0], 0, cls), codec.from_double(v[N], 1, cls),
+            codec.from_double(v[2 * N], 2, cls), codec.from_double(v[3 * N], 3, cls));
     }
 }
 

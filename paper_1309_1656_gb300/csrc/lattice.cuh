@@ -260,30 +260,114 @@ __device__ __forceinline__ unsigned collide_dev(float *d, float *sx, float *sy, 
     return flag;
 }
 
-// Storage codecs: the stored type S, the arithmetic type R, whether the
-// kernels work on deviations d_i = f_i - w_i (DEV) or on f_i itself, and
-// the step kernel's minimum resident blocks per SM (register budget).
+// The four components (f, s_x, s_y, s_z) of one slot at one site are stored
+// together as one vector, so that each slot plane is an array of vectors and
+// a warp's access to it covers 32 consecutive vectors: 512 B in single
+// precision (float4, one 128-bit access per thread), 256 B in half (4
+// halves, one 64-bit access), 1 KB in double (two 128-bit accesses).  A
+// neighbour shift moves by whole vectors, so every access stays aligned.
+struct __align__(16) DQuad {
+    double2 a, b;
+};
+template <class T> struct QuadOf;
+template <> struct QuadOf<double> { using V = DQuad; };
+template <> struct QuadOf<float> { using V = float4; };
+template <> struct QuadOf<__half> { using V = uint2; };
+
+__device__ __forceinline__ void ldq(const DQuad *p, double &f, double &x, double &y, double &z)
+{
+    const double2 a = p->a, b = p->b;
+    f = a.x;
+    x = a.y;
+    y = b.x;
+    z = b.y;
+}
+__device__ __forceinline__ void stq(DQuad *p, double f, double x, double y, double z)
+{
+    p->a = make_double2(f, x);
+    p->b = make_double2(y, z);
+}
+__device__ __forceinline__ void ldq(const float4 *p, float &f, float &x, float &y, float &z)
+{
+    const float4 v = *p;
+    f = v.x;
+    x = v.y;
+    y = v.z;
+    z = v.w;
+}
+__device__ __forceinline__ void stq(float4 *p, float f, float x, float y, float z) { *p = make_float4(f, x, y, z); }
+__device__ __forceinline__ void ldq(const uint2 *p, __half &f, __half &x, __half &y, __half &z)
+{
+    const uint2 v = *p;
+    const __half2 a = *reinterpret_cast<const __half2 *>(&v.x), b = *reinterpret_cast<const __half2 *>(&v.y);
+    f = __low2half(a);
+    x = __high2half(a);
+    y = __low2half(b);
+    z = __high2half(b);
+}
+__device__ __forceinline__ void stq(uint2 *p, __half f, __half x, __half y, __half z)
+{
+    const __half2 a = __halves2half2(f, x), b = __halves2half2(y, z);
+    uint2 v;
+    v.x = *reinterpret_cast<const unsigned *>(&a);
+    v.y = *reinterpret_cast<const unsigned *>(&b);
+    *p = v;
+}
+
+// Storage codecs: the stored type S (vector V of four), the arithmetic type
+// R, whether the kernels work on deviations d_i = f_i - w_i (DEV) or on f_i
+// itself, and the step kernel's minimum resident blocks per SM (register
+// budget).  load4 / store4 move the four components of one slot at one site
+// between storage and arithmetic type.
 // to_double / from_double convert a stored value of component comp (0 = f,
 // 1..3 = s) of a direction of class cls = |i|^2 to and from the value of
 // the population itself, in double.
 struct CodecF64 {
     using S = double;
+    using V = QuadOf<S>::V;
     using R = double;
     static constexpr bool DEV = false;
     static constexpr int MIN_BLOCKS = 1;   // 76 doubles per site need the registers
     __device__ __forceinline__ R load(S v) const { return v; }
     __device__ __forceinline__ S store(R v) const { return v; }
+    __device__ __forceinline__ void load4(const V *p, R &f, R &x, R &y, R &z) const
+    {
+        S a, b, c, d;
+        ldq(p, a, b, c, d);
+        f = load(a);
+        x = load(b);
+        y = load(c);
+        z = load(d);
+    }
+    __device__ __forceinline__ void store4(V *p, R f, R x, R y, R z) const
+    {
+        stq(p, store(f), store(x), store(y), store(z));
+    }
     __device__ __forceinline__ double to_double(R v, int, int) const { return v; }
     __device__ __forceinline__ S from_double(double v, int, int) const { return v; }
 };
 struct CodecF32 {
     using S = float;
+    using V = QuadOf<S>::V;
     using R = float;
     static constexpr bool DEV = true;
     static constexpr int MIN_BLOCKS = 4;   // <= 128 registers: 16 warps per SM
     double fref[3];   // w_i by class: the reference equilibrium's traces
     __device__ __forceinline__ R load(S v) const { return v; }
     __device__ __forceinline__ S store(R v) const { return v; }
+    __device__ __forceinline__ void load4(const V *p, R &f, R &x, R &y, R &z) const
+    {
+        S a, b, c, d;
+        ldq(p, a, b, c, d);
+        f = load(a);
+        x = load(b);
+        y = load(c);
+        z = load(d);
+    }
+    __device__ __forceinline__ void store4(V *p, R f, R x, R y, R z) const
+    {
+        stq(p, store(f), store(x), store(y), store(z));
+    }
     __device__ __forceinline__ double to_double(R v, int comp, int cls) const
     {
         return comp == 0 ? fref[cls] + (double)v : (double)v;
@@ -295,12 +379,26 @@ struct CodecF32 {
 };
 struct CodecF16Dev {
     using S = __half;
+    using V = QuadOf<S>::V;
     using R = float;
     static constexpr bool DEV = true;
     static constexpr int MIN_BLOCKS = 4;
     double fref[3];
     __device__ __forceinline__ R load(S v) const { return __half2float(v); }
     __device__ __forceinline__ S store(R v) const { return __float2half_rn(v); }
+    __device__ __forceinline__ void load4(const V *p, R &f, R &x, R &y, R &z) const
+    {
+        S a, b, c, d;
+        ldq(p, a, b, c, d);
+        f = load(a);
+        x = load(b);
+        y = load(c);
+        z = load(d);
+    }
+    __device__ __forceinline__ void store4(V *p, R f, R x, R y, R z) const
+    {
+        stq(p, store(f), store(x), store(y), store(z));
+    }
     __device__ __forceinline__ double to_double(R v, int comp, int cls) const
     {
         return comp == 0 ? fref[cls] + (double)v : (double)v;
@@ -311,13 +409,13 @@ struct CodecF16Dev {
     }
 };
 
-// Extent and addressing of a lattice: plane stride P (elements) separates
-// the b*4 component planes of the single population buffer.
+// Extent and addressing of a lattice: plane stride P (vectors) separates
+// the b slot planes of the single population buffer.
 struct Grid {
     int nx, ny, nz;
     int nxb;        // blocks per x-row
     int zero;       // always 0 (see k_step_aa)
-    int64_t P;      // plane stride
+    int64_t P;      // plane stride (vectors of four components)
     int64_t N;      // sites
 };
 

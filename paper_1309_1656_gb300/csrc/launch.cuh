@@ -81,9 +81,10 @@ template <int D, class Codec> struct Launchers {
 
     template <class T> static Planes<T, Q> planes_of(const qlbm_ctx *h, const void *base)
     {
+        using V = typename QuadOf<T>::V;
         Planes<T, Q> pl;
-        T *b = static_cast<T *>(const_cast<void *>(base));
-        for (int k = 0; k < 4 * Q; ++k) pl.p[k] = b + (int64_t)k * h->g.P;
+        V *b = static_cast<V *>(const_cast<void *>(base));
+        for (int q = 0; q < Q; ++q) pl.p[q] = b + (int64_t)q * h->g.P;
         return pl;
     }
     static Planes<S, Q> planes(const qlbm_ctx *h) { return planes_of<S>(h, h->pop); }
