@@ -13,6 +13,8 @@ ends with the FP64 conservation reduction.  Reported:
               per site) / its CUDA-event duration, against the measured HBM
               copy bandwidth
   fp64        the same for FP64 storage
+  df64        the same for double-float storage (two floats per value,
+              double-float arithmetic on the FP32 pipes)
   e2e         MLUPS through the C ABI with host buffers: init from pinned
               host fields, K steps, moments back to pinned host memory
   adjoint     reverse sweep time (segment recomputation + adjoint steps) /
@@ -55,7 +57,7 @@ WORKLOADS = {
 
 
 def bytes_per_value(prec):
-    return {"fp64": 8, "fp32": 4, "fp16dev": 2}[prec]
+    return {"fp64": 8, "df64": 8, "fp32": 4, "fp16dev": 2}[prec]
 
 
 def make_fields(w):
@@ -178,6 +180,21 @@ def run_device(lat, K, W, stream, torch):
     return e0.elapsed_time(e1) / K, e0.elapsed_time(e2), cons
 
 
+def max_over_ranks_of(x, ws, device):
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if ws == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(ws, sites_per_rank, steps, seconds):
+    """Whole-job throughput: all ranks' site updates over the slowest time."""
+    return ws * sites_per_rank * steps / seconds / 1e6
+
+
 def bench_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -214,11 +231,7 @@ def bench_ours(args):
             torch.distributed.barrier()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, ws, "cuda")
 
     results = {}
     clocks = None
@@ -237,8 +250,8 @@ def bench_ours(args):
         achieved = alg_bytes / (step_ms * 1e-3) / 1e9
         drift = float(np.max(np.abs(c1 - c0)) / np.max(np.abs(c0)))
         results[prec] = dict(step_ms=step_ms, total_ms=total_ms, achieved=achieved,
-                             mlups=ws * N * K / (total_ms * 1e-3) / 1e6,
-                             kernel_mlups=ws * N / (step_ms * 1e-3) / 1e6, drift=drift,
+                             mlups=job_mlups(ws, N, K, total_ms * 1e-3),
+                             kernel_mlups=job_mlups(ws, N, 1, step_ms * 1e-3), drift=drift,
                              alg_bytes=alg_bytes)
         lat.close()
         del lat
@@ -348,7 +361,7 @@ def bench_ours(args):
         t1 = time.perf_counter()
         dt_e2e = max_over_ranks(t1 - t0)
         lat.close()
-        e2e = {"value": round(ws * N * K / dt_e2e / 1e6, 3), "unit": "MLUPS",
+        e2e = {"value": round(job_mlups(ws, N, K, dt_e2e), 3), "unit": "MLUPS",
                "h2d_bytes_per_step": (r4.nbytes + uu.nbytes) / K,
                "d2h_bytes_per_step": (out_r.nbytes + out_u.nbytes + out_e.nbytes) / K}
 
@@ -377,7 +390,7 @@ def bench_ours(args):
         "metric": METRIC, "value": round(r32["mlups"], 1), "unit": "MLUPS", "n_gpus": ws,
         "steps": K, "warmup": W, "ms_per_step": round(r32["total_ms"] / K, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32"}[prim],
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32", "df64": "f32x2"}[prim],
         "data": "synthetic",
         "config": {"workload": w["desc"], "lattice": "D3Q19" if d == 3 else "D2Q9",
                    "dims": list(dims), "sites": N, "tau": w["tau"], "beta0": w["beta0"],
@@ -419,11 +432,11 @@ def bench_ours(args):
 
 
 def error_growth(w, fl, total, every, torch, qlbm):
-    """Normwise errors of the FP32 and FP16-deviation moment fields against
-    the FP64 run of the same workload, every `every` steps."""
+    """Normwise errors of the double-float, FP32 and FP16-deviation moment
+    fields against the FP64 run of the same workload, every `every` steps."""
     d, dims = w["d"], w["dims"]
     N = dims[0] * dims[1] * dims[2]
-    lats = {p: qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision=p) for p in ("fp64", "fp32", "fp16dev")}
+    lats = {p: qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision=p) for p in ("fp64", "df64", "fp32", "fp16dev")}
     for lat in lats.values():
         lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
     bufs = {p: (torch.empty((4, N), dtype=torch.float64, device="cuda"),
@@ -444,7 +457,7 @@ def error_growth(w, fl, total, every, torch, qlbm):
             return float((a - b_).abs().max() / b_.abs().max())
 
         row = {"step": t}
-        for p in ("fp32", "fp16dev"):
+        for p in ("df64", "fp32", "fp16dev"):
             r, u, e = bufs[p]
             row[p] = {"n": err(r[0], ref[0][0]), "S": err(r[1:], ref[0][1:]), "u": err(u, ref[1]),
                       "eps": err(e, ref[2])}
@@ -527,7 +540,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="d3q19-128", choices=sorted(WORKLOADS))
-    ap.add_argument("--precisions", default="fp32,fp64")
+    ap.add_argument("--precisions", default="fp32,fp64,df64")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -68,8 +68,17 @@ typedef enum qlbm_lattice { QLBM_D2Q9 = 2, QLBM_D3Q19 = 3 } qlbm_lattice;
 /* Storage precision of the populations.  QLBM_FP64 computes in double;
    QLBM_FP32 stores and computes in float; QLBM_FP16_DEV stores the deviation
    W_i - W_i^ref from a uniform reference equilibrium in half precision and
-   computes in float. */
-typedef enum qlbm_precision { QLBM_FP64 = 0, QLBM_FP32 = 1, QLBM_FP16_DEV = 2 } qlbm_precision;
+   computes in float; QLBM_DF64 stores each value as an unevaluated sum of two
+   floats (8 bytes, 48-bit significand) and computes in double-float
+   arithmetic on the single-precision pipes (results within ~1e-14 of double
+   per step; no reverse mode: the adjoint calls return
+   QLBM_ERR_UNSUPPORTED). */
+typedef enum qlbm_precision {
+    QLBM_FP64 = 0,
+    QLBM_FP32 = 1,
+    QLBM_FP16_DEV = 2,
+    QLBM_DF64 = 3
+} qlbm_precision;
 
 typedef enum qlbm_ptr_kind { QLBM_HOST = 0, QLBM_DEVICE = 1 } qlbm_ptr_kind;
 

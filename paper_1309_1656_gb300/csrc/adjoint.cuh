@@ -319,11 +319,7 @@ k_step_push(const Planes<typename Codec::S, Lattice<D>::Q> src, const Planes<typ
     if (!site_of_block(g, si)) return;
     R f[Q], sx[Q], sy[Q], sz[Q];
     gather<D, Codec, false>(src, g, si, codec, f, sx, sy, sz);
-    unsigned flag;
-    if constexpr (Codec::DEV)
-        flag = collide_dev<D>(f, sx, sy, sz, k);
-    else
-        flag = collide<D, R>(f, sx, sy, sz, k);
+    const unsigned flag = Codec::template collide<D>(f, sx, sy, sz, k);
     if constexpr (MAG) rotate_spins<D, R>(sx, sy, sz, k.rot);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {

@@ -217,7 +217,7 @@ int qlbm_create(qlbm_handle *out, int lattice, const int64_t dims[3], double tau
     if (!out || !dims) return fail(nullptr, QLBM_ERR_INVALID_ARG, "null argument");
     if (lattice != QLBM_D2Q9 && lattice != QLBM_D3Q19)
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "lattice must be QLBM_D2Q9 or QLBM_D3Q19");
-    if (precision != QLBM_FP64 && precision != QLBM_FP32 && precision != QLBM_FP16_DEV)
+    if (precision != QLBM_FP64 && precision != QLBM_FP32 && precision != QLBM_FP16_DEV && precision != QLBM_DF64)
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "unknown precision");
     if (!(tau > 0.0) || !(beta0 > 0.0) || !(dt > 0.0))
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "tau, beta0 and dt must be > 0");
@@ -249,7 +249,7 @@ int qlbm_create(qlbm_handle *out, int lattice, const int64_t dims[3], double tau
         delete h;
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "lattice too large for the launch grid");
     }
-    h->elem_bytes = precision == QLBM_FP64 ? 8 : (precision == QLBM_FP32 ? 4 : 2);
+    h->elem_bytes = (precision == QLBM_FP64 || precision == QLBM_DF64) ? 8 : (precision == QLBM_FP32 ? 4 : 2);
 
     cudaError_t e = cudaGetDevice(&h->device);
     size_t bytes = (size_t)h->b * 4 * (size_t)g.P * h->elem_bytes;
@@ -449,6 +449,7 @@ int qlbm_step_adjoint(qlbm_handle h, const double *lam_next, double *lam, double
 {
     if (!valid(h) || !lam_next || !lam) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_step_adjoint: bad argument");
     if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    if (!h->ops->adjoint) return fail(h, QLBM_ERR_UNSUPPORTED, "qlbm_step_adjoint: no reverse mode for this precision");
     int rc = ensure_reverse(h);
     if (rc) return rc;
     const void *state = h->pop;
@@ -473,6 +474,7 @@ int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval)
     if (!valid(h) || nsteps < 0 || interval < 0) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_rollout: bad argument");
     if (h->eq_path != QLBM_EQ_DIRECT)
         return fail(h, QLBM_ERR_UNSUPPORTED, "qlbm_rollout: the reverse mode covers the direct equilibrium path");
+    if (!h->ops->adjoint) return fail(h, QLBM_ERR_UNSUPPORTED, "qlbm_rollout: no reverse mode for this precision");
     int64_t K = interval;
     if (K == 0) {
         K = 1;
@@ -514,6 +516,7 @@ int qlbm_rollout_adjoint(qlbm_handle h, const double *lam_T, double *lam_0, doub
 {
     if (!valid(h) || !lam_T || !lam_0) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_rollout_adjoint: bad argument");
     if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    if (!h->ops->adjoint) return fail(h, QLBM_ERR_UNSUPPORTED, "qlbm_rollout_adjoint: no reverse mode for this precision");
     if (h->ro_steps < 0) return fail(h, QLBM_ERR_STATE, "qlbm_rollout_adjoint: no rollout recorded");
     int rc = ensure_reverse(h);
     if (rc) return rc;

@@ -173,8 +173,9 @@ k_init_fd(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, InitConsts 
     for (int q = 0; q < Q; ++q) {
         const int cls = cnorm2<D>(q);
         const double wp = ic.w[cls] * poly_P_d<D>(ic, q, jx, jy, jz, be);
-        stq(pl.p[q] + s, codec.from_double(wp * n, 0, cls), codec.from_double(wp * Sx, 1, cls),
-            codec.from_double(wp * Sy, 2, cls), codec.from_double(wp * Sz, 3, cls));
+        codec.store4(pl.p[q] + s, codec.load(codec.from_double(wp * n, 0, cls)),
+                     codec.load(codec.from_double(wp * Sx, 1, cls)), codec.load(codec.from_double(wp * Sy, 2, cls)),
+                     codec.load(codec.from_double(wp * Sz, 3, cls)));
     }
 }
 

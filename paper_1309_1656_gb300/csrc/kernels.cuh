@@ -20,6 +20,7 @@
 
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "lattice.cuh"
 
 namespace qlbm {
@@ -92,11 +93,7 @@ k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typena
     if (!site_of_block(g, si)) return;
     R f[Q], sx[Q], sy[Q], sz[Q];
     gather<D, Codec, ODD>(pl, g, si, codec, f, sx, sy, sz);
-    unsigned flag;
-    if constexpr (Codec::DEV)
-        flag = collide_dev<D>(f, sx, sy, sz, k);
-    else
-        flag = collide<D, R>(f, sx, sy, sz, k);
+    const unsigned flag = Codec::template collide<D>(f, sx, sy, sz, k);
     if constexpr (MAG) rotate_spins<D, R>(sx, sy, sz, k.rot);
     // g.zero is 0 at run time; adding it keeps the compiler from carrying the
     // 4b load addresses (identical to the store addresses) through the
@@ -151,8 +148,9 @@ k_init_eq(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, InitConsts 
     for (int q = 0; q < Q; ++q) {
         const int cls = cnorm2<D>(q);
         const double wp = ic.w[cls] * poly_P_d<D>(ic, q, jx, jy, jz, be);
-        stq(pl.p[q] + s, codec.from_double(wp * n, 0, cls), codec.from_double(wp * Sx, 1, cls),
-            codec.from_double(wp * Sy, 2, cls), codec.from_double(wp * Sz, 3, cls));
+        codec.store4(pl.p[q] + s, codec.load(codec.from_double(wp * n, 0, cls)),
+                     codec.load(codec.from_double(wp * Sx, 1, cls)), codec.load(codec.from_double(wp * Sy, 2, cls)),
+                     codec.load(codec.from_double(wp * Sz, 3, cls)));
     }
 }
 
@@ -193,8 +191,9 @@ k_set_state(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec cod
     for (int q = 0; q < Q; ++q) {
         const double *v = in + (int64_t)(4 * q) * N + si.s;
         const int cls = cnorm2<D>(q);
-        stq(pl.p[q] + si.s, codec.from_double(v[0], 0, cls), codec.from_double(v[N], 1, cls),
-            codec.from_double(v[2 * N], 2, cls), codec.from_double(v[3 * N], 3, cls));
+        codec.store4(pl.p[q] + si.s, codec.load(codec.from_double(v[0], 0, cls)),
+                     codec.load(codec.from_double(v[N], 1, cls)), codec.load(codec.from_double(v[2 * N], 2, cls)),
+                     codec.load(codec.from_double(v[3 * N], 3, cls)));
     }
 }
 

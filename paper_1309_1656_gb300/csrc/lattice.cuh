@@ -316,9 +316,9 @@ __device__ __forceinline__ void stq(uint2 *p, __half f, __half x, __half y, __ha
 
 // Storage codecs: the stored type S (vector V of four), the arithmetic type
 // R, whether the kernels work on deviations d_i = f_i - w_i (DEV) or on f_i
-// itself, and the step kernel's minimum resident blocks per SM (register
-// budget).  load4 / store4 move the four components of one slot at one site
-// between storage and arithmetic type.
+// itself, the collision that goes with them, and the step kernel's minimum
+// resident blocks per SM (register budget).  load4 / store4 move the four
+// components of one slot at one site between storage and arithmetic type.
 // to_double / from_double convert a stored value of component comp (0 = f,
 // 1..3 = s) of a direction of class cls = |i|^2 to and from the value of
 // the population itself, in double.
@@ -328,6 +328,10 @@ struct CodecF64 {
     using R = double;
     static constexpr bool DEV = false;
     static constexpr int MIN_BLOCKS = 1;   // 76 doubles per site need the registers
+    template <int D> static __device__ __forceinline__ unsigned collide(R *f, R *x, R *y, R *z, const Coll<R> &k)
+    {
+        return qlbm::collide<D, R>(f, x, y, z, k);
+    }
     __device__ __forceinline__ R load(S v) const { return v; }
     __device__ __forceinline__ S store(R v) const { return v; }
     __device__ __forceinline__ void load4(const V *p, R &f, R &x, R &y, R &z) const
@@ -352,6 +356,10 @@ struct CodecF32 {
     using R = float;
     static constexpr bool DEV = true;
     static constexpr int MIN_BLOCKS = 4;   // <= 128 registers: 16 warps per SM
+    template <int D> static __device__ __forceinline__ unsigned collide(R *f, R *x, R *y, R *z, const Coll<R> &k)
+    {
+        return collide_dev<D>(f, x, y, z, k);
+    }
     double fref[3];   // w_i by class: the reference equilibrium's traces
     __device__ __forceinline__ R load(S v) const { return v; }
     __device__ __forceinline__ S store(R v) const { return v; }
@@ -383,6 +391,10 @@ struct CodecF16Dev {
     using R = float;
     static constexpr bool DEV = true;
     static constexpr int MIN_BLOCKS = 4;
+    template <int D> static __device__ __forceinline__ unsigned collide(R *f, R *x, R *y, R *z, const Coll<R> &k)
+    {
+        return collide_dev<D>(f, x, y, z, k);
+    }
     double fref[3];
     __device__ __forceinline__ R load(S v) const { return __half2float(v); }
     __device__ __forceinline__ S store(R v) const { return __float2half_rn(v); }

@@ -7,6 +7,7 @@
 #include "adjoint.cuh"
 #include "fdkernels.cuh"
 #include "kernels.cuh"
+#include "twopass.cuh"
 
 namespace qlbm {
 
@@ -73,6 +74,12 @@ template <> inline CodecF16Dev make_codec<CodecF16Dev>(const qlbm_ctx *h)
     for (int i = 0; i < 3; ++i) c.fref[i] = h->hc.w[i];
     return c;
 }
+template <> inline CodecDF make_codec<CodecDF>(const qlbm_ctx *h)
+{
+    CodecDF c;
+    c.lo = (int64_t)h->b * h->g.P;
+    return c;
+}
 
 template <int D, class Codec> struct Launchers {
     using S = typename Codec::S;
@@ -95,6 +102,20 @@ template <int D, class Codec> struct Launchers {
         const Planes<S, Q> pl = planes(h);
         const Coll<R> k = make_coll<R>(h);
         const Codec codec = make_codec<Codec>(h);
+        if constexpr (TwoPass<Codec>::value) {
+            if (h->mag) {
+                if (odd)
+                    k_step_aa_df2<D, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+                else
+                    k_step_aa_df2<D, false, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+            } else {
+                if (odd)
+                    k_step_aa_df2<D, true, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+                else
+                    k_step_aa_df2<D, false, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+            }
+            return cudaGetLastError();
+        }
         if (h->mag) {
             if (odd)
                 k_step_aa<D, Codec, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
@@ -272,14 +293,24 @@ template <int D, class Codec> struct Launchers {
         return cudaGetLastError();
     }
 
+    // The reverse mode (adjoint, push, cotangent import/export) exists for
+    // the FP64, FP32 and FP16 codecs; double-float storage is forward only.
     static const LatticeOps *table()
     {
-        static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
-                                     &conserved_partial, &adjoint, &push, &copy_natural, &lam_import,
-                                     &lam_export, &init_adjoint, &fd_params,
-                                     std::is_same<Codec, CodecF64>::value ? &step_fd : nullptr,
-                                     &fd_params_adjoint, &init_fd};
-        return &t;
+        if constexpr (std::is_same<Codec, CodecDF>::value) {
+            static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
+                                         &conserved_partial, nullptr, nullptr, &copy_natural, nullptr,
+                                         nullptr, &init_adjoint, &fd_params, nullptr,
+                                         &fd_params_adjoint, &init_fd};
+            return &t;
+        } else {
+            static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
+                                         &conserved_partial, &adjoint, &push, &copy_natural, &lam_import,
+                                         &lam_export, &init_adjoint, &fd_params,
+                                         std::is_same<Codec, CodecF64>::value ? &step_fd : nullptr,
+                                         &fd_params_adjoint, &init_fd};
+            return &t;
+        }
     }
 };
 
@@ -289,6 +320,7 @@ template <int D> const LatticeOps *ops_for(int prec)
     case QLBM_FP64: return Launchers<D, CodecF64>::table();
     case QLBM_FP32: return Launchers<D, CodecF32>::table();
     case QLBM_FP16_DEV: return Launchers<D, CodecF16Dev>::table();
+    case QLBM_DF64: return Launchers<D, CodecDF>::table();
     default: return nullptr;
     }
 }
