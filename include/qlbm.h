@@ -197,6 +197,24 @@ int qlbm_set_magnetic_field(qlbm_handle h, double mu, const double B[3]);
 int qlbm_fd_params(qlbm_handle h, double *beta, double *mu_up, double *mu_dn, double *axis,
                    int64_t *nfail, int ptr_kind);
 
+/* qlbm_step_fd_output -- one time step (exactly as qlbm_step(h, 1)) that also
+ * writes the Fermi-Dirac parameters of the state it started from (Sec. 2.2,
+ * Prop. 1; the collision conserves the moments they depend on), fused into
+ * the step kernel: the same solve as qlbm_fd_params in single precision
+ * (in double only where the single-precision iteration does not settle).
+ * Parameters to ~1e-5 relative; the spin splitting mu_up - mu_dn to ~1e-6
+ * |mu| absolute, so near degenerate eigenvalues (|S| << tr rho) use
+ * qlbm_fd_params, which solves and returns double.  QLBM_FP32 and
+ * QLBM_FP16_DEV storage, direct equilibrium path (QLBM_ERR_UNSUPPORTED
+ * otherwise).
+ *   beta, mu_up, mu_dn  float [N];  axis float [3][N] (zero where |S| = 0);
+ *   all required, all on one side (ptr_kind).  Sites without a solution get
+ *   NaN; their count is written to *nfail if nfail is not NULL.
+ * Asynchronous for device pointers with nfail == NULL; synchronising
+ * otherwise. */
+int qlbm_step_fd_output(qlbm_handle h, float *beta, float *mu_up, float *mu_dn, float *axis, int64_t *nfail,
+                        int ptr_kind);
+
 /* qlbm_init_fd_params -- equilibrium initial state from physical Fermi-Dirac
  * parameters (Sec. 2.2), as the paper sets up its Riemann problem: per site
  * n_s = (2 pi/beta)^(d/2) F_{d/2-1}(beta mu_s) (Eq. nFDstdOmega), eps from

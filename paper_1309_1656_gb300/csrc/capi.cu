@@ -668,6 +668,49 @@ int qlbm_fd_params(qlbm_handle h, double *beta, double *mu_up, double *mu_dn, do
     return check_flags(h);
 }
 
+int qlbm_step_fd_output(qlbm_handle h, float *beta, float *mu_up, float *mu_dn, float *axis, int64_t *nfail,
+                        int ptr_kind)
+{
+    if (!valid(h) || !beta || !mu_up || !mu_dn || !axis)
+        return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_step_fd_output: null argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    if (!h->ops->step_fdout)
+        return fail(h, QLBM_ERR_UNSUPPORTED, "qlbm_step_fd_output: needs QLBM_FP32 or QLBM_FP16_DEV storage");
+    if (h->eq_path != QLBM_EQ_DIRECT)
+        return fail(h, QLBM_ERR_UNSUPPORTED, "qlbm_step_fd_output: covers the direct equilibrium path");
+    if (!h->fd_fail) CK(h, cudaMalloc(&h->fd_fail, sizeof(unsigned long long)));
+    const size_t N = (size_t)h->g.N;
+    float *b = beta, *mu = mu_up, *md = mu_dn, *ax = axis;
+    if (ptr_kind == QLBM_HOST) {
+        int rc = ensure_staging(h, 6 * N * sizeof(float));
+        if (rc) return rc;
+        b = reinterpret_cast<float *>(h->staging);
+        mu = b + N;
+        md = mu + N;
+        ax = md + N;
+    }
+    const bool count = nfail != nullptr;
+    if (count) CK(h, cudaMemsetAsync(h->fd_fail, 0, sizeof(unsigned long long), h->stream));
+    CK(h, h->ops->step_fdout(h, h->parity == 1, b, mu, md, ax));
+    h->parity ^= 1;
+    h->t += 1;
+    h->ro_steps = -1;
+    if (ptr_kind == QLBM_HOST) {
+        CK(h, cudaMemcpyAsync(beta, b, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaMemcpyAsync(mu_up, mu, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaMemcpyAsync(mu_dn, md, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaMemcpyAsync(axis, ax, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (count || ptr_kind == QLBM_HOST) {
+        unsigned long long nf = 0;
+        if (count) CK(h, cudaMemcpyAsync(&nf, h->fd_fail, sizeof(nf), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (count) *nfail = (int64_t)nf;
+        return check_flags(h);
+    }
+    return QLBM_OK;
+}
+
 int qlbm_fd_params_adjoint(qlbm_handle h, const double *g_beta, const double *g_mu_up, const double *g_mu_dn,
                            const double *g_axis, double *lam, int ptr_kind)
 {

@@ -246,4 +246,45 @@ k_step_aa_fd(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<double> k, FdA
     if (flag) atomicOr(flags, flag);
 }
 
+// One single-precision AA step (the step kernel's collision and addressing,
+// bit for bit) that also writes the Fermi-Dirac parameters of the state it
+// started from: after the stores, the site's conserved moments (which the
+// collision leaves unchanged) go through the single-precision solve
+// (fd_params_site_f; double near degenerate eigenvalues).  The solve runs
+// while the stores drain.  Outputs float [N] (axis [3][N]).
+template <int D, class Codec, bool ODD, bool MAG>
+__global__ void __launch_bounds__(kStepBlock, Codec::MIN_BLOCKS)
+k_step_aa_fdout(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<float> k, Codec codec,
+                float beta0, unsigned *__restrict__ flags, float *__restrict__ beta, float *__restrict__ mu_up,
+                float *__restrict__ mu_dn, float *__restrict__ axis, unsigned long long *__restrict__ nfail)
+{
+    constexpr int Q = Lattice<D>::Q;
+    SiteIdx si;
+    if (!site_of_block(g, si)) return;
+    float f[Q], sx[Q], sy[Q], sz[Q];
+    gather<D, Codec, ODD>(pl, g, si, codec, f, sx, sy, sz);
+    float mom[5];
+    const unsigned flag = collide_dev<D, true>(f, sx, sy, sz, k, mom);
+    if constexpr (MAG) rotate_spins<D, float>(sx, sy, sz, k.rot);
+    SiteIdx so = si;
+    so.s += g.zero;
+    so.x += g.zero;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int slot = ODD ? q : opposite<D>(q);
+        const int s = ODD ? neighbour(g, so, cx<D>(q), cy<D>(q), cz<D>(q)) : so.s;
+        codec.store4(pl.p[slot] + s, f[q], sx[q], sy[q], sz[q]);
+    }
+    if (flag) atomicOr(flags, flag);
+    const FdParamsF p = fd_params_site_f<D>(mom[0], mom[1], mom[2], mom[3], mom[4] / beta0);
+    const int64_t N = g.N, s = si.s;
+    beta[s] = p.beta;
+    mu_up[s] = p.mu_up;
+    mu_dn[s] = p.mu_dn;
+    axis[s] = p.ax;
+    axis[N + s] = p.ay;
+    axis[2 * N + s] = p.az;
+    if (p.status != 0) atomicAdd(nfail, 1ull);
+}
+
 }  // namespace qlbm

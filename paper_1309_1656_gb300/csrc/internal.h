@@ -92,6 +92,8 @@ struct LatticeOps {
                                      const double *gmu_dn, const double *gaxis, double *lam);
     cudaError_t (*init_fd)(qlbm_ctx *h, const double *beta, const double *mu_up, const double *mu_dn,
                            const double *axis, const double *u);
+    // single-precision step that also writes the FD parameters (FP32 / FP16 storage; NULL otherwise)
+    cudaError_t (*step_fdout)(qlbm_ctx *h, bool odd, float *beta, float *mu_up, float *mu_dn, float *axis);
 };
 
 const LatticeOps *lattice_ops_d2q9(int prec);

@@ -171,9 +171,11 @@ __device__ __forceinline__ unsigned collide(R *f, R *sx, R *sy, R *sz, const Col
 // g_i -= w_i (A + B.i + C |i|^2) (which only shifts the base coefficients
 // and adds one linear term); the rest population then takes the exact mass
 // and spin balance.  What remains is unbiased rounding.
-template <int D>
+// With MOM, mom receives the site's n, S_x, S_y, S_z and beta0 eps (the
+// conserved moments the equilibrium was built from).
+template <int D, bool MOM = false>
 __device__ __forceinline__ unsigned collide_dev(float *d, float *sx, float *sy, float *sz,
-                                                const Coll<float> &k)
+                                                const Coll<float> &k, float *mom = nullptr)
 {
     constexpr int Q = Lattice<D>::Q;
     constexpr int REST = (Q - 1) / 2;
@@ -254,6 +256,13 @@ __device__ __forceinline__ unsigned collide_dev(float *d, float *sx, float *sy, 
     sx[REST] = Sx - xr;
     sy[REST] = Sy - yr;
     sz[REST] = Sz - zr;
+    if constexpr (MOM) {
+        mom[0] = n;
+        mom[1] = Sx;
+        mom[2] = Sy;
+        mom[3] = Sz;
+        mom[4] = fmaf(k.K, de - jj, k.c);   // beta0 eps = c + K (de - |j|^2)
+    }
     unsigned flag = 0u;
     if (!(n > 0.f)) flag |= (n == n) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;
     if (!(fabsf(Sx) + fabsf(Sy) + fabsf(Sz) + fabsf(de) < 1e30f)) flag |= FLAG_NONFINITE;

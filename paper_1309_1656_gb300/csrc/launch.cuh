@@ -293,6 +293,31 @@ template <int D, class Codec> struct Launchers {
         return cudaGetLastError();
     }
 
+    static cudaError_t step_fdout(qlbm_ctx *h, bool odd, float *beta, float *mu_up, float *mu_dn, float *axis)
+    {
+        if constexpr (Codec::DEV) {
+            const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+            const Planes<S, Q> pl = planes(h);
+            const Coll<R> k = make_coll<R>(h);
+            const Codec codec = make_codec<Codec>(h);
+            const float b0 = (float)h->hc.beta0;
+#define QLBM_FDOUT(ODD, MAG)                                                                                   \
+    k_step_aa_fdout<D, Codec, ODD, MAG><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, b0, h->flags, beta, mu_up, \
+                                                                    mu_dn, axis, h->fd_fail)
+            if (h->mag) {
+                if (odd) QLBM_FDOUT(true, true);
+                else QLBM_FDOUT(false, true);
+            } else {
+                if (odd) QLBM_FDOUT(true, false);
+                else QLBM_FDOUT(false, false);
+            }
+#undef QLBM_FDOUT
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
+
     // The reverse mode (adjoint, push, cotangent import/export) exists for
     // the FP64, FP32 and FP16 codecs; double-float storage is forward only.
     static const LatticeOps *table()
@@ -301,14 +326,14 @@ template <int D, class Codec> struct Launchers {
             static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
                                          &conserved_partial, nullptr, nullptr, &copy_natural, nullptr,
                                          nullptr, &init_adjoint, &fd_params, nullptr,
-                                         &fd_params_adjoint, &init_fd};
+                                         &fd_params_adjoint, &init_fd, nullptr};
             return &t;
         } else {
             static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
                                          &conserved_partial, &adjoint, &push, &copy_natural, &lam_import,
                                          &lam_export, &init_adjoint, &fd_params,
                                          std::is_same<Codec, CodecF64>::value ? &step_fd : nullptr,
-                                         &fd_params_adjoint, &init_fd};
+                                         &fd_params_adjoint, &init_fd, Codec::DEV ? &step_fdout : nullptr};
             return &t;
         }
     }

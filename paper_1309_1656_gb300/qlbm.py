@@ -74,6 +74,7 @@ _rollout_adjoint = _sig("qlbm_rollout_adjoint", _i, [_vp, _vp, _vp, ctypes.POINT
 _init_adjoint = _sig("qlbm_init_equilibrium_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i])
 _fd_params = _sig("qlbm_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64), _i])
 _fd_params_adjoint = _sig("qlbm_fd_params_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
+_step_fd_output = _sig("qlbm_step_fd_output", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64), _i])
 _init_fd = _sig("qlbm_init_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
 _set_field = _sig("qlbm_set_magnetic_field", _i, [_vp, _d, ctypes.POINTER(_d)])
 _set_eq_path = _sig("qlbm_set_equilibrium_path", _i, [_vp, _i])
@@ -107,6 +108,20 @@ def _ptr(a, kind=None):
     import torch
     if a.dtype != torch.float64 or not a.is_contiguous():
         raise TypeError("device tensors must be contiguous float64")
+    return a.data_ptr(), QLBM_DEVICE
+
+
+def _ptr32(a):
+    """(pointer, ptr_kind) of a float32 numpy array or CUDA tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("host arrays must be C-contiguous float32")
+        return a.ctypes.data, QLBM_HOST
+    if not getattr(a, "is_cuda", False):
+        raise TypeError("expected a numpy array or a CUDA tensor")
+    import torch
+    if a.dtype != torch.float32 or not a.is_contiguous():
+        raise TypeError("device tensors must be contiguous float32")
     return a.data_ptr(), QLBM_DEVICE
 
 
@@ -216,6 +231,16 @@ def qlbm_fd_params(h, beta=None, mu_up=None, mu_dn=None, axis=None):
     nf = _i64(0)
     _check(_fd_params(h, *[x[0] for x in p], ctypes.byref(nf), _kind(*p)), h)
     return nf.value
+
+
+def qlbm_step_fd_output(h, beta, mu_up, mu_dn, axis, count=True):
+    """One step that also writes the float32 FD parameters of the state it
+    started from; returns the number of unresolved sites (None if not
+    counted, which keeps device calls asynchronous)."""
+    p = [_ptr32(beta), _ptr32(mu_up), _ptr32(mu_dn), _ptr32(axis)]
+    nf = _i64(0)
+    _check(_step_fd_output(h, *[x[0] for x in p], ctypes.byref(nf) if count else None, _kind(*p)), h)
+    return nf.value if count else None
 
 
 def qlbm_fd_params_adjoint(h, lam, g_beta=None, g_mu_up=None, g_mu_dn=None, g_axis=None):
@@ -333,6 +358,16 @@ class Lattice:
         mu_dn = np.zeros(self.N)
         axis = np.zeros((3, self.N))
         nfail = qlbm_fd_params(self.h, beta, mu_up, mu_dn, axis)
+        return beta, mu_up, mu_dn, axis, nfail
+
+    def step_fd_output(self):
+        """One step; returns the float32 FD parameters (beta, mu_up, mu_dn,
+        axis, nfail) of the state it started from."""
+        beta = np.zeros(self.N, np.float32)
+        mu_up = np.zeros(self.N, np.float32)
+        mu_dn = np.zeros(self.N, np.float32)
+        axis = np.zeros((3, self.N), np.float32)
+        nfail = qlbm_step_fd_output(self.h, beta, mu_up, mu_dn, axis)
         return beta, mu_up, mu_dn, axis, nfail
 
     def set_magnetic_field(self, mu, B):

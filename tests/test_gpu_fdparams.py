@@ -205,3 +205,58 @@ def test_init_from_fd_parameters(q, oracle_mod, d, dims, prec, tol):
         q.qlbm_init_fd_params(lat.h, beta, mu_up, mu_dn, axis, u)
         got = lat.get_state()
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16dev"])
+@pytest.mark.parametrize("d,dims", [(2, (37, 29, 1)), (3, (33, 6, 4))])
+def test_step_fd_output_state_equals_plain_step(q, prec, d, dims):
+    # the fused kernel runs the step kernel's collision and addressing: the
+    # state after it is the state after a plain step, in both AA parities
+    fl = fields.random_fields(d, dims, seed=21)
+    with q.Lattice(d, dims, 0.7, 1.0, precision=prec) as a, q.Lattice(d, dims, 0.7, 1.0, precision=prec) as b:
+        for lat in (a, b):
+            lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+            lat.step(3)
+        for _ in range(2):
+            a.step(1)
+            out = b.step_fd_output()
+            assert out[4] == 0
+            assert np.array_equal(a.get_state(), b.get_state())
+        assert a.time() == b.time() == 5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16dev"])
+@pytest.mark.parametrize("d,dims", [(2, (48, 40, 1)), (3, (16, 14, 12))])
+def test_step_fd_output_params_vs_double_solve(q, prec, d, dims):
+    # single-precision solve fused into the step against the double solve of
+    # the same state (qlbm_fd_params); a quarter of the sites are near
+    # degenerate (|S| < 0.005 n), where the float splitting keeps ~1e-6 |mu|
+    fl = fields.modes(d, dims, seed=17, amp=0.05, umax=0.1)
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(5)
+    deg = rng.random(N) < 0.25
+    fl["rho4"][1:, deg] *= rng.uniform(0.0, 0.005, deg.sum()) / np.maximum(
+        np.linalg.norm(fl["rho4"][1:, deg], axis=0) / fl["rho4"][0, deg], 1e-300)
+    with q.Lattice(d, dims, 0.7, 1.0, precision=prec) as lat:
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        lat.step(2)
+        b64, mu64, md64, ax64, nf64 = lat.fd_params()
+        b, mu, md, ax, nf = lat.step_fd_output()
+    assert nf == 0 and nf64 == 0
+    assert np.allclose(b, b64, rtol=2e-5, atol=0)
+    scale = 1.0 / b64
+    assert np.all(np.abs(mu - mu64) <= 2e-5 * (np.abs(mu64) + scale))
+    assert np.all(np.abs(md - md64) <= 2e-5 * (np.abs(md64) + scale))
+    # spin splitting, including the near-degenerate sites
+    split64 = mu64 - md64
+    assert np.all(np.abs((mu - md) - split64) <= 1e-4 * np.abs(split64) + 2e-6 * scale)
+    S = np.linalg.norm(fl["rho4"][1:], axis=0)
+    ok = S > 0
+    assert np.allclose(ax[:, ok], ax64[:, ok], atol=2e-5)
+
+
+def test_step_fd_output_needs_single_precision_storage(q):
+    with q.Lattice(2, (8, 6, 1), 0.7, 1.0, precision="fp64") as lat:
+        lat.init_equilibrium(np.r_[np.ones((1, 48)), np.zeros((3, 48))], np.zeros((2, 48)))
+        with pytest.raises(q.QLBMError):
+            lat.step_fd_output()
