@@ -17,6 +17,13 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def oracle_mod():
+    # QLBM_ORACLE_DIR names a directory holding a (deliberately altered) copy
+    # of the oracle package; the mutation tests run the pins against it.
+    alt = os.environ.get("QLBM_ORACLE_DIR")
+    if alt:
+        sys.path.insert(0, alt)
     import oracle
+    if alt:
+        assert os.path.dirname(os.path.dirname(os.path.abspath(oracle.__file__))) == os.path.abspath(alt)
     oracle.build()
     return oracle
