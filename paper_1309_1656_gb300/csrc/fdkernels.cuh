@@ -253,7 +253,7 @@ k_step_aa_fd(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<double> k, FdA
 // (fd_params_site_f; double near degenerate eigenvalues).  The solve runs
 // while the stores drain.  Outputs float [N] (axis [3][N]).
 template <int D, class Codec, bool ODD, bool MAG>
-__global__ void __launch_bounds__(kStepBlock, Codec::MIN_BLOCKS)
+__global__ void __launch_bounds__(kStepBlock, step_min_blocks<D, Codec>())
 k_step_aa_fdout(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<float> k, Codec codec,
                 float beta0, unsigned *__restrict__ flags, float *__restrict__ beta, float *__restrict__ mu_up,
                 float *__restrict__ mu_dn, float *__restrict__ axis, unsigned long long *__restrict__ nfail)

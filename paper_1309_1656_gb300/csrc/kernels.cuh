@@ -82,8 +82,15 @@ __device__ __forceinline__ void gather(const Planes<typename Codec::S, Lattice<D
 
 // One AA step (even: ODD = false, odd: ODD = true), fused
 // moments + equilibrium + collision + streaming.
+// Minimum resident blocks of 128 per SM for the step kernels (register
+// budget), by lattice.
+template <int D, class Codec> constexpr int step_min_blocks()
+{
+    return D == 2 ? Codec::MIN_BLOCKS_2D : Codec::MIN_BLOCKS;
+}
+
 template <int D, class Codec, bool ODD, bool MAG = false>
-__global__ void __launch_bounds__(kStepBlock, Codec::MIN_BLOCKS)
+__global__ void __launch_bounds__(kStepBlock, step_min_blocks<D, Codec>())
 k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typename Codec::R> k,
           Codec codec, unsigned *__restrict__ flags)
 {

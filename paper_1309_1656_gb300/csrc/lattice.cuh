@@ -337,6 +337,7 @@ struct CodecF64 {
     using R = double;
     static constexpr bool DEV = false;
     static constexpr int MIN_BLOCKS = 1;   // 76 doubles per site need the registers
+    static constexpr int MIN_BLOCKS_2D = MIN_BLOCKS;
     template <int D> static __device__ __forceinline__ unsigned collide(R *f, R *x, R *y, R *z, const Coll<R> &k)
     {
         return qlbm::collide<D, R>(f, x, y, z, k);
@@ -365,6 +366,7 @@ struct CodecF32 {
     using R = float;
     static constexpr bool DEV = true;
     static constexpr int MIN_BLOCKS = 4;   // <= 128 registers: 16 warps per SM
+    static constexpr int MIN_BLOCKS_2D = MIN_BLOCKS;
     template <int D> static __device__ __forceinline__ unsigned collide(R *f, R *x, R *y, R *z, const Coll<R> &k)
     {
         return collide_dev<D>(f, x, y, z, k);
@@ -400,6 +402,7 @@ struct CodecF16Dev {
     using R = float;
     static constexpr bool DEV = true;
     static constexpr int MIN_BLOCKS = 4;
+    static constexpr int MIN_BLOCKS_2D = 6;   // D2Q9: 36 values per site fit in 80 registers
     template <int D> static __device__ __forceinline__ unsigned collide(R *f, R *x, R *y, R *z, const Coll<R> &k)
     {
         return collide_dev<D>(f, x, y, z, k);
@@ -407,18 +410,25 @@ struct CodecF16Dev {
     double fref[3];
     __device__ __forceinline__ R load(S v) const { return __half2float(v); }
     __device__ __forceinline__ S store(R v) const { return __float2half_rn(v); }
+    // pairs convert in one instruction each way (half2 <-> float2); the
+    // rounding is the same round-to-nearest as __float2half_rn per value
     __device__ __forceinline__ void load4(const V *p, R &f, R &x, R &y, R &z) const
     {
-        S a, b, c, d;
-        ldq(p, a, b, c, d);
-        f = load(a);
-        x = load(b);
-        y = load(c);
-        z = load(d);
+        const uint2 v = *p;
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+        f = a.x;
+        x = a.y;
+        y = b.x;
+        z = b.y;
     }
     __device__ __forceinline__ void store4(V *p, R f, R x, R y, R z) const
     {
-        stq(p, store(f), store(x), store(y), store(z));
+        const __half2 a = __floats2half2_rn(f, x), b = __floats2half2_rn(y, z);
+        uint2 v;
+        v.x = *reinterpret_cast<const unsigned *>(&a);
+        v.y = *reinterpret_cast<const unsigned *>(&b);
+        *p = v;
     }
     __device__ __forceinline__ double to_double(R v, int comp, int cls) const
     {
