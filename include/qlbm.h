@@ -84,8 +84,9 @@ typedef enum qlbm_ptr_kind { QLBM_HOST = 0, QLBM_DEVICE = 1 } qlbm_ptr_kind;
 
 typedef struct qlbm_ctx *qlbm_handle;
 
-/* qlbm_create -- set up a lattice (Sec. 3.3: "The framework takes as input the
- * relaxation time tau and a reference inverse temperature beta0").
+/* qlbm_create -- set up a lattice (Sec. 3.3: the scheme's inputs are the
+ * relaxation time tau and the reference inverse temperature beta0 of the
+ * quadrature).
  *   out        receives the handle (unchanged on failure)
  *   lattice    QLBM_D2Q9 or QLBM_D3Q19
  *   dims       {nx, ny, nz}; nz must be 1 for D2Q9; every entry >= 1
@@ -237,7 +238,7 @@ int qlbm_fd_params_adjoint(qlbm_handle h, const double *g_beta, const double *g_
                            const double *g_mu_dn, const double *g_axis, double *lam, int ptr_kind);
 
 /* Equilibrium path of qlbm_step.  QLBM_EQ_DIRECT (default): W_i^eq = w_i rho
- * P_i (Eq. WeqAlgo; "the unitary matrix U ... does not need to be computed").
+ * P_i (Eq. WeqAlgo: only rho enters, U is never formed).
  * QLBM_EQ_FD_PARAMS: W_i^eq = w_i U diag(n_up, n_dn) U* P_i (Eq. WeqDiscr)
  * with U, beta, mu_s recovered per site as in qlbm_fd_params and
  * n_s = (2 pi/beta)^(d/2) F_{d/2-1}(beta mu_s); it agrees with the direct path

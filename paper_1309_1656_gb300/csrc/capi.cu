@@ -249,6 +249,10 @@ int qlbm_create(qlbm_handle *out, int lattice, const int64_t dims[3], double tau
         delete h;
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "lattice too large for the launch grid");
     }
+    if (g.P > 0x7fffffffLL) {   // the kernels index sites with 32-bit integers
+        delete h;
+        return fail(nullptr, QLBM_ERR_INVALID_ARG, "lattice too large: at most 2^31 - 64 sites");
+    }
     h->elem_bytes = (precision == QLBM_FP64 || precision == QLBM_DF64) ? 8 : (precision == QLBM_FP32 ? 4 : 2);
 
     cudaError_t e = cudaGetDevice(&h->device);

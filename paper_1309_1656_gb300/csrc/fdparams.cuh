@@ -4,8 +4,8 @@
 //
 // Given the site's density matrix rho = (n 1 + S.sigma)/2 and internal energy
 // eps: the analytic 2x2 eigen-decomposition gives the occupations
-// n_up/dn = (n +- |S|)/2 and the Bloch axis S/|S| of U (Sec. 2.2, "U ... can
-// be recovered by diagonalizing rho"); then (beta, nu_up, nu_dn), nu = beta mu,
+// n_up/dn = (n +- |S|)/2 and the Bloch axis S/|S| of U (Sec. 2.2: U is the
+// eigenbasis of rho); then (beta, nu_up, nu_dn), nu = beta mu,
 // solve
 //   n_s = (2 pi/beta)^h F_{h-1}(nu_s),   n eps = h beta^-1 (2 pi/beta)^h sum_s F_h(nu_s),
 // h = d/2.  The three equations are solved together by Newton's method on

@@ -47,7 +47,11 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     for kw in (dict(lattice=5, dims=(4, 4, 1)), dict(lattice=2, dims=(4, 4, 2)),
                dict(lattice=3, dims=(0, 4, 4)), dict(lattice=2, dims=(4, 4, 1), tau=-1.0),
                dict(lattice=2, dims=(4, 4, 1), beta0=0.0),
-               dict(lattice=2, dims=(4, 4, 1), precision=7)):
+               dict(lattice=2, dims=(4, 4, 1), precision=7),
+               # 2^32 sites: beyond the kernels' 32-bit site index (155 GB in
+               # FP16 at 2^31 would still fit the device, so this must be caught)
+               dict(lattice=2, dims=(65536, 65536, 1), precision=2),
+               dict(lattice=3, dims=(1024, 1024, 2048), precision=2)):
         args = dict(tau=0.8, beta0=1.0, dt=1.0, precision=0)
         args.update(kw)
         with pytest.raises(qlbm.QLBMError) as e:
