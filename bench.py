@@ -71,7 +71,7 @@ def make_fields(w):
     raise ValueError(w["kind"])
 
 
-STEP_KERNEL_SOURCES = ("lattice.cuh", "kernels.cuh")
+STEP_KERNEL_SOURCES = ("lattice.cuh", "step.cuh")
 
 
 def kernel_source_hash(files=STEP_KERNEL_SOURCES):

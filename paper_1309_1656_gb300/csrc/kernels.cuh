@@ -1,122 +1,15 @@
-// CUDA kernels of the forward path, templated on the lattice (D = 2: D2Q9,
-// D = 3: D3Q19) and the storage codec.  Instantiated once per lattice in
+// CUDA kernels of the forward path besides the step (step.cuh): initial
+// equilibrium, state exchange, moments and the conservation sums; templated
+// on the lattice and the storage codec.  Instantiated once per lattice in
 // kernels_d2q9.cu / kernels_d3q19.cu.
-//
-// Memory layout (HBM): one population buffer of b slot planes, plane q
-// holding, for every site, the vector of the four components (f, s_x, s_y,
-// s_z) of slot q; plane stride P >= N vectors (padded to 64), site
-// s = x + nx*(y + ny*z).  Streaming is done in
-// place with the AA pattern (Bailey et al., 2009):
-//   even step:  read slot q at x              -> population q at x,
-//               write population q' to slot opposite(q') at x;
-//   odd step:   read slot q at x + e_q        -> population opposite(q) at x,
-//               write population q' to slot q' at x + e_q'.
-// Each thread reads and writes the same b*4 locations, so the update is
-// race-free in one buffer and every value is read once and written once per
-// step (Eq. TransportStep).  After an even step the buffer is "swapped"
-// (population q at x sits in slot opposite(q) at x - e_q); after an odd step
-// it is back in natural order.
 #pragma once
 
 #include <type_traits>
 
 #include "dfloat.cuh"
-#include "lattice.cuh"
+#include "step.cuh"
 
 namespace qlbm {
-
-constexpr int kStepBlock = 128;   // threads per block along x
-constexpr int kRedBlock = 256;    // threads per block of the reductions
-
-// Base pointers of the b slot planes (vectors of the four components of
-// storage type S), passed by value so that every access is one multiply-add
-// of a 32-bit site index onto a constant-bank pointer (keeps the b addresses
-// out of registers).
-template <class S, int Q> struct Planes {
-    typename QuadOf<S>::V *p[Q];
-};
-
-// Site of the calling thread; false if it lies beyond the row.
-struct SiteIdx {
-    int x, y, z;
-    int s;   // flat site index (N < 2^31)
-};
-
-__device__ __forceinline__ bool site_of_block(const Grid &g, SiteIdx &si)
-{
-    const int row = blockIdx.x / g.nxb;
-    const int xb = blockIdx.x - row * g.nxb;
-    si.x = xb * blockDim.x + threadIdx.x;
-    si.y = row % g.ny;
-    si.z = row / g.ny;
-    si.s = row * g.nx + si.x;
-    return si.x < g.nx;
-}
-
-// Flat index of site x + (dx,dy,dz), periodic.
-__device__ __forceinline__ int neighbour(const Grid &g, const SiteIdx &si, int dx, int dy, int dz)
-{
-    const int x = wrapm(si.x + dx, g.nx);
-    const int y = wrapm(si.y + dy, g.ny);
-    const int z = wrapm(si.z + dz, g.nz);
-    return x + g.nx * (y + g.ny * z);
-}
-
-// Gathers the b populations of site si at the current time, in arithmetic
-// type R.  SWAPPED selects the reading pattern of a buffer last written by
-// an even step.
-template <int D, class Codec, bool SWAPPED>
-__device__ __forceinline__ void gather(const Planes<typename Codec::S, Lattice<D>::Q> &pl,
-                                       const Grid &g, const SiteIdx &si, const Codec &codec,
-                                       typename Codec::R *f, typename Codec::R *sx,
-                                       typename Codec::R *sy, typename Codec::R *sz)
-{
-    constexpr int Q = Lattice<D>::Q;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int p = SWAPPED ? opposite<D>(q) : q;     // population held by slot q
-        const int s = SWAPPED ? neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q)) : si.s;
-        codec.load4(pl.p[q] + s, f[p], sx[p], sy[p], sz[p]);
-    }
-}
-
-// One AA step (even: ODD = false, odd: ODD = true), fused
-// moments + equilibrium + collision + streaming.
-// Minimum resident blocks of 128 per SM for the step kernels (register
-// budget), by lattice.
-template <int D, class Codec> constexpr int step_min_blocks()
-{
-    return D == 2 ? Codec::MIN_BLOCKS_2D : Codec::MIN_BLOCKS;
-}
-
-template <int D, class Codec, bool ODD, bool MAG = false>
-__global__ void __launch_bounds__(kStepBlock, step_min_blocks<D, Codec>())
-k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typename Codec::R> k,
-          Codec codec, unsigned *__restrict__ flags)
-{
-    using R = typename Codec::R;
-    constexpr int Q = Lattice<D>::Q;
-    SiteIdx si;
-    if (!site_of_block(g, si)) return;
-    R f[Q], sx[Q], sy[Q], sz[Q];
-    gather<D, Codec, ODD>(pl, g, si, codec, f, sx, sy, sz);
-    const unsigned flag = Codec::template collide<D>(f, sx, sy, sz, k);
-    if constexpr (MAG) rotate_spins<D, R>(sx, sy, sz, k.rot);
-    // g.zero is 0 at run time; adding it keeps the compiler from carrying the
-    // 4b load addresses (identical to the store addresses) through the
-    // collision in registers.
-    SiteIdx so = si;
-    so.s += g.zero;
-    so.x += g.zero;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        // population q goes to slot opposite(q) at x (even) or slot q at x + e_q (odd)
-        const int slot = ODD ? q : opposite<D>(q);
-        const int s = ODD ? neighbour(g, so, cx<D>(q), cy<D>(q), cz<D>(q)) : so.s;
-        codec.store4(pl.p[slot] + s, f[q], sx[q], sy[q], sz[q]);
-    }
-    if (flag) atomicOr(flags, flag);
-}
 
 // ---------------------------------------------------------------------------
 // Initial equilibrium (Eq. WeqAlgo evaluated from given rho, u, eps), in
@@ -267,6 +160,36 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double *__restr
     }
 }
 
+// Block sum of values held by lane 0 of each warp (other lanes hold 0).
+template <int NV>
+__device__ __forceinline__ void block_sum_lanes0(const double (&v)[NV], double *__restrict__ out)
+{
+    __shared__ double sh[kRedBlock / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[warp][i] = v[i];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double acc = 0.0;
+        for (int w = 0; w < kRedBlock / 32; ++w) acc += sh[w][threadIdx.x];
+        out[threadIdx.x] = acc;
+    }
+}
+
+// Per thread, the sites' sums go into double-float accumulators on the
+// FP32 pipes for single-precision and double-float storage (GB300's FP64
+// pipe issues 1/64 as fast, and converting and adding every population in
+// double made this reduction FP64-bound at ~10 % of HBM bandwidth): each
+// site's eight sums are formed exactly in double-float (TwoSum of the
+// single-precision values, or of the double-float pairs), added to the
+// thread's running double-float totals, and only those totals are converted
+// to double after a double-float warp sum.  The deviation codecs'
+// reference part (sum over q of the fref terms, times N) is added once.
+// FP64 storage sums in double.
+__device__ __forceinline__ df as_df(float v) { return df(v, 0.f); }
+__device__ __forceinline__ df as_df(df v) { return v; }
+
 template <int D, class Codec, bool SWAPPED>
 __global__ void __launch_bounds__(kRedBlock)
 k_conserved_partial(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec codec,
@@ -276,28 +199,89 @@ k_conserved_partial(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, C
     constexpr int Q = Lattice<D>::Q;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
-        SiteIdx si;
-        si.s = (int)s;
-        si.x = (int)(s % g.nx);
-        const int64_t row = s / g.nx;
-        si.y = (int)(row % g.ny);
-        si.z = (int)(row / g.ny);
-        R f[Q], sx[Q], sy[Q], sz[Q];
-        gather<D, Codec, SWAPPED>(pl, g, si, codec, f, sx, sy, sz);
+    if constexpr (std::is_same<R, double>::value) {
+        for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+            SiteIdx si;
+            si.s = (int)s;
+            si.x = (int)(s % g.nx);
+            const int64_t row = s / g.nx;
+            si.y = (int)(row % g.ny);
+            si.z = (int)(row / g.ny);
+            R f[Q], sx[Q], sy[Q], sz[Q];
+            gather<D, Codec, SWAPPED>(pl, g, si, codec, f, sx, sy, sz);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int cls = cnorm2<D>(q);
-            const double fq = codec.to_double(f[q], 0, cls);
-            acc[0] += fq;
-            acc[1] += codec.to_double(sx[q], 1, cls);
-            acc[2] += codec.to_double(sy[q], 2, cls);
-            acc[3] += codec.to_double(sz[q], 3, cls);
-            acc[4] += cx<D>(q) * fq;
-            acc[5] += cy<D>(q) * fq;
-            acc[6] += cz<D>(q) * fq;
-            acc[7] += cnorm2<D>(q) * fq;
+            for (int q = 0; q < Q; ++q) {
+                const int cls = cnorm2<D>(q);
+                const double fq = codec.to_double(f[q], 0, cls);
+                acc[0] += fq;
+                acc[1] += codec.to_double(sx[q], 1, cls);
+                acc[2] += codec.to_double(sy[q], 2, cls);
+                acc[3] += codec.to_double(sz[q], 3, cls);
+                acc[4] += cx<D>(q) * fq;
+                acc[5] += cy<D>(q) * fq;
+                acc[6] += cz<D>(q) * fq;
+                acc[7] += cnorm2<D>(q) * fq;
+            }
         }
+    } else {
+        df tot[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tot[k] = df(0.f, 0.f);
+        for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+            SiteIdx si;
+            si.s = (int)s;
+            si.x = (int)(s % g.nx);
+            const int64_t row = s / g.nx;
+            si.y = (int)(row % g.ny);
+            si.z = (int)(row / g.ny);
+            R f[Q], sx[Q], sy[Q], sz[Q];
+            gather<D, Codec, SWAPPED>(pl, g, si, codec, f, sx, sy, sz);
+            DFAcc a[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k].set(df(0.f, 0.f));
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const df fq = as_df(f[q]);
+                a[0].add(fq);
+                a[1].add(as_df(sx[q]));
+                a[2].add(as_df(sy[q]));
+                a[3].add(as_df(sz[q]));
+                if (cx<D>(q)) a[4].add(cx<D>(q) > 0 ? fq : -fq);
+                if (cy<D>(q)) a[5].add(cy<D>(q) > 0 ? fq : -fq);
+                if (cz<D>(q)) a[6].add(cz<D>(q) > 0 ? fq : -fq);
+                if (cnorm2<D>(q)) a[7].add(scale2(fq, (float)cnorm2<D>(q)));
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) tot[k] = tot[k] + a[k].value();
+        }
+        // warp sum in double-float, then one conversion per warp
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            for (int o = 16; o > 0; o >>= 1) {
+                const df other(__shfl_down_sync(0xffffffffu, tot[k].hi, o), __shfl_down_sync(0xffffffffu, tot[k].lo, o));
+                tot[k] = tot[k] + other;
+            }
+            acc[k] = (threadIdx.x & 31) == 0 ? tot[k].to_double() : 0.0;
+        }
+        // reference part of a deviation codec (to_double(0, comp, cls) per
+        // value), N times, once for the whole lattice
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            double ref[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int cls = cnorm2<D>(q);
+                const double r = codec.to_double(R(0), 0, cls);
+                ref[0] += r;
+                ref[4] += cx<D>(q) * r;
+                ref[5] += cy<D>(q) * r;
+                ref[6] += cz<D>(q) * r;
+                ref[7] += cnorm2<D>(q) * r;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] += (double)g.N * ref[k];
+        }
+        block_sum_lanes0<8>(acc, partials + (int64_t)blockIdx.x * 8);
+        return;
     }
     block_sum_store<8>(acc, partials + (int64_t)blockIdx.x * 8);
 }
