@@ -176,3 +176,57 @@ def test_autograd_spin_magnetisation_gradient(q):
         assert ad == pytest.approx(fd, rel=1e-4, abs=1e-6)
     fdt = (J64(fl["rho4"], tau + h) - J64(fl["rho4"], tau - h)) / (2 * h)
     assert g_tau == pytest.approx(fdt, rel=1e-3, abs=1e-6)
+
+
+def test_autograd_momentum_flux_gradient(q, oracle_mod):
+    # observable: the momentum flux Pi_xy = sum_i e_ix e_iy tr W_i summed over
+    # a box after T FP32 steps; gradient with respect to the initial density,
+    # velocity and internal-energy fields and tau, against central
+    # differences of FP64 forward runs (h = 1e-5)
+    import torch
+    from paper_1309_1656_gb300.autograd import rollout
+    d, dims, T, tau, beta0 = 2, (40, 36, 1), 30, 0.75, 1.0
+    N = int(np.prod(dims))
+    fl = fields.random_fields(d, dims, seed=31)
+    c = oracle_mod.constants(d, beta0)
+    xi = c["xi"]
+    idx = c["idx"]
+    wxy = torch.tensor([xi * xi * i[0] * i[1] for i in idx], dtype=torch.float64, device="cuda")
+    box = np.zeros((dims[1], dims[0]), bool)
+    box[10:26, 12:30] = True
+    box = box.ravel()
+    mask = torch.from_numpy(box).cuda()
+    rho4 = torch.from_numpy(fl["rho4"]).cuda().requires_grad_(True)
+    u = torch.from_numpy(fl["u"]).cuda().requires_grad_(True)
+    eps = torch.from_numpy(fl["eps"]).cuda().requires_grad_(True)
+    tau_t = torch.tensor(tau, dtype=torch.float64, device="cuda", requires_grad=True)
+    with q.Lattice(d, dims, tau, beta0, precision="fp32") as lat:
+        state = rollout(lat, rho4, u, eps, tau_t, T)
+        J = (wxy[:, None] * state[:, 0, :])[:, mask].sum()
+        J.backward()
+    grads = {"rho4": rho4.grad.cpu().numpy(), "u": u.grad.cpu().numpy(), "eps": eps.grad.cpu().numpy()}
+    g_tau = float(tau_t.grad)
+    w_np = wxy.cpu().numpy()
+
+    def J64(r4, uu, ee, t):
+        with q.Lattice(d, dims, t, beta0, precision="fp64") as l64:
+            l64.init_equilibrium(r4, uu, ee)
+            l64.step(T)
+            st = l64.get_state()
+        return float((w_np[:, None] * st[:, 0, :])[:, box].sum())
+
+    rng = np.random.default_rng(77)
+    h = 1e-5
+    base = {k: fl[k] for k in ("rho4", "u", "eps")}
+    for name in ("rho4", "u", "eps"):
+        dv = rng.normal(size=base[name].shape)
+        p = dict(base)
+        m = dict(base)
+        p[name] = base[name] + h * dv
+        m[name] = base[name] - h * dv
+        fd = (J64(p["rho4"], p["u"], p["eps"], tau) - J64(m["rho4"], m["u"], m["eps"], tau)) / (2 * h)
+        ad = float(np.sum(grads[name] * dv))
+        assert ad == pytest.approx(fd, rel=2e-4, abs=1e-7), name
+    fdt = (J64(base["rho4"], base["u"], base["eps"], tau + h) -
+           J64(base["rho4"], base["u"], base["eps"], tau - h)) / (2 * h)
+    assert g_tau == pytest.approx(fdt, rel=2e-4, abs=1e-7)
