@@ -236,7 +236,7 @@ int qlbm_create(qlbm_handle *out, int lattice, const int64_t dims[3], double tau
     h->stream = static_cast<cudaStream_t>(stream);
     compute_constants(d, beta0, &h->hc);
     h->b = h->hc.b;
-    h->ops = (d == 2) ? lattice_ops_d2q9(precision) : lattice_ops_d3q19(precision);
+    h->ops = lattice_ops(d, precision);
     Grid &g = h->g;
     g.nx = (int)dims[0];
     g.ny = (int)dims[1];

@@ -96,8 +96,26 @@ struct LatticeOps {
     cudaError_t (*step_fdout)(qlbm_ctx *h, bool odd, float *beta, float *mu_up, float *mu_dn, float *axis);
 };
 
-const LatticeOps *lattice_ops_d2q9(int prec);
-const LatticeOps *lattice_ops_d3q19(int prec);
+// Dispatch tables, one translation unit each (kernels_<lattice>_<codec>.cu).
+const LatticeOps *ops_d2q9_fp64();
+const LatticeOps *ops_d2q9_fp32();
+const LatticeOps *ops_d2q9_fp16();
+const LatticeOps *ops_d2q9_df64();
+const LatticeOps *ops_d3q19_fp64();
+const LatticeOps *ops_d3q19_fp32();
+const LatticeOps *ops_d3q19_fp16();
+const LatticeOps *ops_d3q19_df64();
+
+inline const LatticeOps *lattice_ops(int d, int prec)
+{
+    switch (prec) {
+    case QLBM_FP64: return d == 2 ? ops_d2q9_fp64() : ops_d3q19_fp64();
+    case QLBM_FP32: return d == 2 ? ops_d2q9_fp32() : ops_d3q19_fp32();
+    case QLBM_FP16_DEV: return d == 2 ? ops_d2q9_fp16() : ops_d3q19_fp16();
+    case QLBM_DF64: return d == 2 ? ops_d2q9_df64() : ops_d3q19_df64();
+    default: return nullptr;
+    }
+}
 
 cudaError_t launch_conserved_final(qlbm_ctx *h);
 

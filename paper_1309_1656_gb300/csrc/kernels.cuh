@@ -1,7 +1,7 @@
 // CUDA kernels of the forward path besides the step (step.cuh): initial
 // equilibrium, state exchange, moments and the conservation sums; templated
-// on the lattice and the storage codec.  Instantiated once per lattice in
-// kernels_d2q9.cu / kernels_d3q19.cu.
+// on the lattice and the storage codec.  Instantiated once per lattice and
+// codec in kernels_<lattice>_<codec>.cu.
 #pragma once
 
 #include <type_traits>

@@ -1,0 +1,8 @@
+// D2Q9 (Sec. 3.1, d = 2, b = 9) kernels for FP64 storage: the dispatch table of one lattice and one
+// storage codec, in a translation unit of its own so the instantiations
+// compile in parallel.
+#include "launch.cuh"
+
+namespace qlbm {
+const LatticeOps *ops_d2q9_fp64() { return Launchers<2, CodecF64>::table(); }
+}  // namespace qlbm

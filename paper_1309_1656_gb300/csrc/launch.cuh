@@ -1,6 +1,6 @@
-// Host launchers of the forward kernels for one lattice, gathered into a
-// dispatch table per storage precision.  Included by exactly one translation
-// unit per lattice.
+// Host launchers of the kernels for one lattice and one storage codec,
+// gathered into a dispatch table (Launchers<D, Codec>::table()).  Each
+// kernels_<lattice>_<codec>.cu instantiates one of them.
 #pragma once
 
 #include "internal.h"
@@ -338,16 +338,5 @@ template <int D, class Codec> struct Launchers {
         }
     }
 };
-
-template <int D> const LatticeOps *ops_for(int prec)
-{
-    switch (prec) {
-    case QLBM_FP64: return Launchers<D, CodecF64>::table();
-    case QLBM_FP32: return Launchers<D, CodecF32>::table();
-    case QLBM_FP16_DEV: return Launchers<D, CodecF16Dev>::table();
-    case QLBM_DF64: return Launchers<D, CodecDF>::table();
-    default: return nullptr;
-    }
-}
 
 }  // namespace qlbm

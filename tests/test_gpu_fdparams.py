@@ -209,12 +209,16 @@ def test_init_from_fd_parameters(q, oracle_mod, d, dims, prec, tol):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16dev"])
 @pytest.mark.parametrize("d,dims", [(2, (37, 29, 1)), (3, (33, 6, 4))])
-def test_step_fd_output_state_equals_plain_step(q, prec, d, dims):
-    # the fused kernel runs the step kernel's collision and addressing: the
-    # state after it is the state after a plain step, in both AA parities
+@pytest.mark.parametrize("field", [False, True])
+def test_step_fd_output_state_equals_plain_step(q, prec, d, dims, field):
+    # the fused kernel runs the step kernel's collision and addressing (and
+    # the field's spin rotation): the state after it is the state after a
+    # plain step, in both AA parities
     fl = fields.random_fields(d, dims, seed=21)
     with q.Lattice(d, dims, 0.7, 1.0, precision=prec) as a, q.Lattice(d, dims, 0.7, 1.0, precision=prec) as b:
         for lat in (a, b):
+            if field:
+                lat.set_magnetic_field(0.3, (0.4, -0.25, 0.9))
             lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
             lat.step(3)
         for _ in range(2):
@@ -260,3 +264,24 @@ def test_step_fd_output_needs_single_precision_storage(q):
         lat.init_equilibrium(np.r_[np.ones((1, 48)), np.zeros((3, 48))], np.zeros((2, 48)))
         with pytest.raises(q.QLBMError):
             lat.step_fd_output()
+
+
+def test_step_fd_output_device_pointers_match_host(q):
+    # device float32 tensors (asynchronous when not counting) and host arrays
+    # give the same parameters and the same state
+    import torch
+    d, dims = 3, (20, 9, 7)
+    N = int(np.prod(dims))
+    fl = fields.modes(d, dims, seed=23)
+    with q.Lattice(d, dims, 0.7, 1.0, precision="fp32") as a, q.Lattice(d, dims, 0.7, 1.0, precision="fp32") as b:
+        for lat in (a, b):
+            lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        host = a.step_fd_output()
+        dev = [torch.empty(N, dtype=torch.float32, device="cuda") for _ in range(3)]
+        ax = torch.empty((3, N), dtype=torch.float32, device="cuda")
+        assert q.qlbm_step_fd_output(b.h, *dev, ax, count=False) is None
+        b.sync()
+        for x, y in zip(host[:3], dev):
+            assert np.array_equal(x, y.cpu().numpy())
+        assert np.array_equal(host[3], ax.cpu().numpy())
+        assert np.array_equal(a.get_state(), b.get_state())
