@@ -124,12 +124,23 @@ cudaError_t launch_conserved_final(qlbm_ctx *h);
 int set_global_error(int code, const char *msg);
 
 // Launch shape of the per-site kernels: one thread per site, blocks of up to
-// kStepBlock consecutive x in one row.
-inline dim3 site_block(const Grid &g)
+// kStepBlock consecutive x in one row.  Rows longer than 128 take the width
+// among 128, 96 and 64 that leaves the fewest idle threads at the row's end
+// (ties to the wider block): e.g. 96 for nx = 192, 64 for nx = 320.
+inline int site_block_width(int nx)
 {
-    int bx = g.nx >= 128 ? 128 : ((g.nx + 31) / 32) * 32;
-    return dim3(bx);
+    if (nx <= 128) return ((nx + 31) / 32) * 32;
+    int best = 128, idle = (128 - nx % 128) % 128;
+    for (int bx = 96; bx >= 64; bx -= 32) {
+        const int id = (bx - nx % bx) % bx;
+        if (id < idle) {
+            best = bx;
+            idle = id;
+        }
+    }
+    return best;
 }
+inline dim3 site_block(const Grid &g) { return dim3(site_block_width(g.nx)); }
 inline dim3 site_grid(const Grid &g, int bx)
 {
     return dim3((unsigned)((int64_t)g.nxb * g.ny * g.nz));
