@@ -405,9 +405,27 @@ def bench_ours(args):
             torch.distributed.destroy_process_group()
         return
 
+    def parity(sdims, sfl, nsteps, st_ref, mom_ref):
+        """Errors of the GPU precisions against the oracle on the CPU sample
+        (normwise, max |x - x_ref| / max |x_ref|)."""
+        err = lambda a, b_: float(np.max(np.abs(a - b_)) / np.max(np.abs(b_)))
+        res = {"steps": nsteps, "norm": "max |x - x_oracle| / max |x_oracle|"}
+        for prec in ("fp64", "df64", "fp32", "fp16dev"):
+            with qlbm.Lattice(d, sdims, w["tau"], w["beta0"], precision=prec) as lat:
+                lat.init_equilibrium(sfl["rho4"], sfl["u"], sfl["eps"])
+                lat.step(nsteps)
+                r4, uu, ee = lat.moments()
+                e = {"n": err(r4[0], mom_ref[0][0]), "S": err(r4[1:], mom_ref[0][1:]),
+                     "u": err(uu, mom_ref[1]), "eps": err(ee, mom_ref[2])}
+                if prec in ("fp64", "df64"):
+                    e["state"] = err(lat.get_state(), st_ref)
+                    e["state_per_step"] = e["state"] / nsteps
+                res[prec] = {k: float("%.3g" % v) for k, v in e.items()}
+        return res
+
     cpu = None
     if ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(w, target_s=args.cpu_seconds)
+        cpu = cpu_baseline(w, target_s=args.cpu_seconds, parity_fn=parity)
 
     r32 = results.get("fp32") or next(iter(results.values()))
     prim = "fp32" if "fp32" in results else next(iter(results))
@@ -510,8 +528,10 @@ def cpu_sample(w, L=32):
     return dims, fl
 
 
-def cpu_baseline(w, target_s=15.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+def cpu_baseline(w, target_s=15.0, parity_fn=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload.
+    With parity_fn, the GPU precisions run the same sample for 1000 steps
+    and report their error against the oracle's result."""
     import oracle
     oracle.build()
     d = w["d"]
@@ -528,9 +548,14 @@ def cpu_baseline(w, target_s=15.0):
         dt += time.perf_counter() - t
         n += chunk
         chunk = min(2 * chunk, 4096)
-    return {"value": round(N * n / dt / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": "%s sub-lattice %s of the same workload recipe, %d FP64 steps, %.1f s" %
-                      ("D3Q19" if d == 3 else "D2Q9", "x".join(map(str, dims)), n, dt)}
+    out = {"value": round(N * n / dt / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": "%s sub-lattice %s of the same workload recipe, %d FP64 steps, %.1f s" %
+                     ("D3Q19" if d == 3 else "D2Q9", "x".join(map(str, dims)), n, dt)}
+    if parity_fn is not None:   # 1000 steps: the fields have not yet relaxed away
+        st = oracle.init_equilibrium(d, dims, w["beta0"], fl["rho4"], fl["u"], fl["eps"])
+        st = oracle.run(d, dims, w["tau"], w["beta0"], 1000, st)
+        out["parity"] = parity_fn(dims, fl, 1000, st, oracle.moments(d, dims, w["beta0"], st))
+    return out
 
 
 def bench_reference(args):
