@@ -103,9 +103,10 @@ __device__ __forceinline__ df dfma(df a, df b, df c)
 }
 
 // The collision of `collide` in double-float arithmetic (CodecDF), in three
-// pieces so that a kernel can stream the populations through the moment
-// sums (df_accumulate), form the per-site coefficients (df_coefficients) and
-// update a direction together with its opposite (df_pair):
+// pieces so that the two-pass kernel can stream the populations through the
+// moment sums (df_accumulate), form the per-site coefficients
+// (df_coefficients) and update a direction together with its opposite
+// (df_pair):
 // W' = (1 - omega) W + omega w_i P_i rho, with P_{+-} = bq + c4 t^2 +- c3 t
 // for the pair's t = +-(i.j).
 // A running sum of double-float terms: the hi parts are added exactly
@@ -260,35 +261,15 @@ __device__ __forceinline__ void df_pair(const DFCoef &c, const Coll<df> &k, int 
     }
 }
 
-template <int D>
-__device__ __forceinline__ unsigned collide_df(df *f, df *sx, df *sy, df *sz, const Coll<df> &k)
-{
-    constexpr int Q = Lattice<D>::Q;
-    DFSums a;
-    a.zero();
-#pragma unroll
-    for (int q = 0; q < Q; ++q) df_accumulate<D>(a, q, f[q], sx[q], sy[q], sz[q]);
-    const DFCoef c = df_coefficients<D>(a, k);
-#pragma unroll
-    for (int q = 0; q <= (Q - 1) / 2; ++q)
-        df_pair<D>(c, k, q, f[q], sx[q], sy[q], sz[q], f[Q - 1 - q], sx[Q - 1 - q], sy[Q - 1 - q], sz[Q - 1 - q]);
-    return c.flag;
-}
-
-// Double-float storage and arithmetic: each value a pair of floats
-// (8 bytes, like a double; 48-bit significand) in the split hi / lo layout
-// above, the collision in double-float (collide_df).
+// Double-float storage: each value a pair of floats (8 bytes, like a
+// double; 48-bit significand) in the split hi / lo layout above.  Its step
+// is the two-pass kernel of twopass.cuh (df_accumulate, df_coefficients,
+// df_pair); the codec itself only moves values.
 struct CodecDF {
     using S = df;
     using V = QuadOf<S>::V;
     using R = df;
     static constexpr bool DEV = false;
-    static constexpr int MIN_BLOCKS = 1;
-    static constexpr int MIN_BLOCKS_2D = 1;
-    template <int D> static __device__ __forceinline__ unsigned collide(R *f, R *x, R *y, R *z, const Coll<R> &k)
-    {
-        return collide_df<D>(f, x, y, z, k);
-    }
     int64_t lo;   // float4 elements from a hi vector to its lo vector (b x plane stride)
     __device__ __forceinline__ R load(S v) const { return v; }
     __device__ __forceinline__ S store(R v) const { return v; }

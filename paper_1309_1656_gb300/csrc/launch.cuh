@@ -114,9 +114,7 @@ template <int D, class Codec> struct Launchers {
                 else
                     k_step_aa_df2<D, false, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
             }
-            return cudaGetLastError();
-        }
-        if (h->mag) {
+        } else if (h->mag) {
             if (odd)
                 k_step_aa<D, Codec, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
             else
