@@ -121,8 +121,8 @@ const char *qlbm_last_error(qlbm_handle h);
 int qlbm_info(qlbm_handle h, double *out, int n);
 
 /* qlbm_init_equilibrium -- initial state W_i(x,t0) = W_i^eq(rho(x), u(x),
- * eps(x)) of Eq. WeqAlgo at every site (the paper's input "an initial
- * configuration of distribution functions", Sec. 3.3).
+ * eps(x)) of Eq. WeqAlgo at every site (Sec. 3.3: the scheme starts from
+ * given populations at t0).
  *   rho4  [4][N] Pauli density (tr rho must be > 0)
  *   u     [d][N] velocity
  *   eps   [N] internal energy, or NULL for eps0, the internal energy of the
@@ -165,8 +165,8 @@ int qlbm_get_state(qlbm_handle h, double *buf, int ptr_kind);
 int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
 
 /* qlbm_set_magnetic_field -- adds the Vlasov commutator of an external
- * magnetic field, -i[mu sigma.B, W] (Sec. 5, Eq. sigmaB_comm), "to the
- * collision operator": integrated exactly over each time step it is
+ * magnetic field, -i[mu sigma.B, W] (Sec. 5, Eq. sigmaB_comm), as part of
+ * the collision: integrated exactly over each time step it is
  * W_i -> U W_i U*, U = exp(-i mu dt sigma.B), a rotation of every Bloch
  * vector s_i by 2 mu |B| dt about B.  The field is uniform; it commutes with
  * the SU(2)-covariant collision, so it is applied to the post-collision
