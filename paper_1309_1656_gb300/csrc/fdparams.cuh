@@ -221,6 +221,141 @@ template <int D> __device__ __forceinline__ Fd3 fd3(double x)
     return r;
 }
 
+// Single-precision F_{h-2}, F_{h-1}, F_h from the float tables FDF_*
+// (truncated where the dropped terms are below ~1e-9 relative).
+template <int NT, int K0, int NK>
+__device__ __forceinline__ void fd_series_ntf(float q, float *out)
+{
+    float acc[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) acc[k] = 0.f;
+#pragma unroll
+    for (int n = NT - 1; n >= 0; --n) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            acc[k] = fmaf(q, acc[k], (n & 1) ? -FDF_SERIES[K0 + k][n] : FDF_SERIES[K0 + k][n]);
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) out[k] = q * acc[k];
+}
+
+// q = e^x, x <= -1; 2 q^NT below 1e-8 relative: 3 terms for x <= -8, 7 for
+// x <= -3, else 20.
+template <int K0, int NK>
+__device__ __forceinline__ void fd_seriesf(float x, float q, float *out)
+{
+    if (x <= -8.f) fd_series_ntf<3, K0, NK>(q, out);
+    else if (x <= -3.f) fd_series_ntf<7, K0, NK>(q, out);
+    else fd_series_ntf<FDF_NSER, K0, NK>(q, out);
+}
+
+struct Fd3f {
+    float m2, m1, h;
+};
+
+template <int D> __device__ __forceinline__ Fd3f fd3f(float x)
+{
+    Fd3f r;
+    if (D == 2) {
+        float o[1];
+        if (x <= -1.f) {
+            const float q = expf(x);
+            r.m2 = q / (1.f + q);
+            r.m1 = log1pf(q);
+            fd_seriesf<3, 1>(x, q, o);
+            r.h = o[0];
+        } else if (x < 1.f) {
+            const float e = expf(x);
+            r.m2 = e / (1.f + e);
+            r.m1 = log1pf(e);
+            float acc = 0.f;
+            for (int j = FDF_NTAY - 1; j >= 0; --j) acc = fmaf(x, acc, FDF_TAYLOR[3][j]);
+            r.h = acc;
+        } else {
+            const float q = expf(-x);
+            r.m2 = 1.f / (1.f + q);
+            r.m1 = x + log1pf(q);
+            fd_seriesf<3, 1>(-x, q, o);
+            r.h = 0.5f * x * x + 1.64493407f - o[0];
+        }
+        return r;
+    }
+    float o[3];
+    if (x <= -1.f) {
+        fd_seriesf<0, 3>(x, expf(x), o);
+    } else if (x < 1.f) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float acc = 0.f;
+            for (int j = FDF_NTAY - 1; j >= 0; --j) acc = fmaf(x, acc, FDF_TAYLOR[k][j]);
+            o[k] = acc;
+        }
+    } else if (x < FD_X0 + FD_NINT * FD_WIDTH) {
+        const int i = (int)((x - FD_X0) / FD_WIDTH);
+        const float a = FD_X0 + FD_WIDTH * i;
+        const float t = (x - a - 0.5f * FD_WIDTH) / (0.5f * FD_WIDTH);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float *c = FDF_CHEB[k][i];
+            float b1 = 0.f, b2 = 0.f;
+            for (int j = FDF_NCHEB - 1; j >= 1; --j) {
+                const float b0 = fmaf(2.f * t, b1, c[j] - b2);
+                b2 = b1;
+                b1 = b0;
+            }
+            o[k] = fmaf(t, b1, c[0] - b2);
+        }
+    } else {
+        const float r2 = 1.f / (x * x), sq = sqrtf(x);
+        const float xp[3] = {sq, x * sq, x * x * sq};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float acc = 0.f;
+            for (int n = FDF_NASYM - 1; n >= 1; --n) acc = fmaf(r2, acc, FDF_ASYM[k][n]);
+            o[k] = xp[k] * FDF_ASYM[k][0] * fmaf(r2, acc, 1.f);
+        }
+    }
+    r.m2 = o[0];
+    r.m1 = o[1];
+    r.h = o[2];
+    return r;
+}
+
+// The Newton iteration of fd_params_site in single precision, from the
+// classical start: true and (t = log beta, nu_up, nu_dn) to ~1e-6 when it
+// settles within 20 iterations.
+template <int D>
+__device__ bool fd_newton_f(float nup, float ndn, float n, float eps, float &t, float &nu1, float &nu2)
+{
+    constexpr float h = 0.5f * D;
+    constexpr float hl2pi = h * 1.83787707f;   // h log 2 pi
+    if (!(ndn > 0.f) || !(eps > 0.f) || !(n * eps > 0.f)) return false;
+    const float lA = logf(nup), lB = logf(ndn), lC = logf(n * eps / h);
+    t = logf(h / eps);
+    nu1 = lA - hl2pi + h * t;
+    nu2 = lB - hl2pi + h * t;
+    for (int it = 0; it < 20; ++it) {
+        const Fd3f F1 = fd3f<D>(nu1), F2 = fd3f<D>(nu2);
+        const float sFh = F1.h + F2.h;
+        const float r1 = logf(F1.m1) - h * t + hl2pi - lA;
+        const float r2 = logf(F2.m1) - h * t + hl2pi - lB;
+        const float r3 = logf(sFh) - (h + 1.f) * t + hl2pi - lC;
+        const float ig1 = F1.m1 / F1.m2, ig2 = F2.m1 / F2.m2;
+        const float c1 = F1.m1 / sFh, c2 = F2.m1 / sFh;
+        const float den = -(h + 1.f) + h * (c1 * ig1 + c2 * ig2);
+        float dt = (c1 * ig1 * r1 + c2 * ig2 * r2 - r3) / den;
+        if (!(dt == dt)) return false;
+        dt = fmaxf(-1.f, fminf(1.f, dt));
+        const float d1 = fmaxf(-10.f, fminf(10.f, (h * dt - r1) * ig1));
+        const float d2 = fmaxf(-10.f, fminf(10.f, (h * dt - r2) * ig2));
+        t += dt;
+        nu1 += d1;
+        nu2 += d2;
+        if (fmaxf(fabsf(dt), fmaxf(fabsf(d1), fabsf(d2))) <= 4e-6f * (1.f + fabsf(nu1))) return true;
+    }
+    return false;
+}
+
 // The nested solve (bracketed Newton on log beta around the per-species
 // inversion); the fallback of fd_params_site.
 template <int D>
@@ -328,6 +463,14 @@ __device__ FdParams fd_params_site(double n, double Sx, double Sy, double Sz, do
     const double lA = log(nup), lB = split ? log(ndn) : lA, lC = log(n * eps / h);
     double t = log(h / eps);
     double nu1 = lA - hl2pi + h * t, nu2 = lB - hl2pi + h * t;
+    // start from the single-precision solution (~1e-6) where it settles: two
+    // double iterations then reach rounding level instead of four
+    float tf, n1f, n2f;
+    if (fd_newton_f<D>((float)nup, (float)ndn, (float)n, (float)eps, tf, n1f, n2f)) {
+        t = tf;
+        nu1 = n1f;
+        nu2 = split ? (double)n2f : nu1;
+    }
     Fd3 F1, F2;
     bool settled = false;
     for (int it = 0;; ++it) {
@@ -365,112 +508,14 @@ __device__ FdParams fd_params_site(double n, double Sx, double Sy, double Sz, do
 }
 
 // ---------------------------------------------------------------------------
-// Single-precision solve (the same Newton iteration on the logarithmic
-// system, float tables FDF_*).  Parameters come out to ~1e-6 relative; the
+// Single-precision solve (fd_newton_f, float tables FDF_*).  Parameters come
+// out to ~1e-6 relative; the
 // spin splitting mu_up - mu_dn, a difference of two solved numbers, to
 // ~1e-6 |mu| absolute -- what float outputs can hold (a double solve would
 // not survive their rounding).  Sites where the float iteration does not
 // settle, and invalid ones, go through the double solve (fd_params_site),
 // which also decides their status.
 // ---------------------------------------------------------------------------
-template <int NT, int K0, int NK>
-__device__ __forceinline__ void fd_series_ntf(float q, float *out)
-{
-    float acc[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) acc[k] = 0.f;
-#pragma unroll
-    for (int n = NT - 1; n >= 0; --n) {
-#pragma unroll
-        for (int k = 0; k < NK; ++k)
-            acc[k] = fmaf(q, acc[k], (n & 1) ? -FDF_SERIES[K0 + k][n] : FDF_SERIES[K0 + k][n]);
-    }
-#pragma unroll
-    for (int k = 0; k < NK; ++k) out[k] = q * acc[k];
-}
-
-// q = e^x, x <= -1; 2 q^NT below 1e-8 relative: 3 terms for x <= -8, 7 for
-// x <= -3, else 20.
-template <int K0, int NK>
-__device__ __forceinline__ void fd_seriesf(float x, float q, float *out)
-{
-    if (x <= -8.f) fd_series_ntf<3, K0, NK>(q, out);
-    else if (x <= -3.f) fd_series_ntf<7, K0, NK>(q, out);
-    else fd_series_ntf<FDF_NSER, K0, NK>(q, out);
-}
-
-struct Fd3f {
-    float m2, m1, h;
-};
-
-template <int D> __device__ __forceinline__ Fd3f fd3f(float x)
-{
-    Fd3f r;
-    if (D == 2) {
-        float o[1];
-        if (x <= -1.f) {
-            const float q = expf(x);
-            r.m2 = q / (1.f + q);
-            r.m1 = log1pf(q);
-            fd_seriesf<3, 1>(x, q, o);
-            r.h = o[0];
-        } else if (x < 1.f) {
-            const float e = expf(x);
-            r.m2 = e / (1.f + e);
-            r.m1 = log1pf(e);
-            float acc = 0.f;
-            for (int j = FDF_NTAY - 1; j >= 0; --j) acc = fmaf(x, acc, FDF_TAYLOR[3][j]);
-            r.h = acc;
-        } else {
-            const float q = expf(-x);
-            r.m2 = 1.f / (1.f + q);
-            r.m1 = x + log1pf(q);
-            fd_seriesf<3, 1>(-x, q, o);
-            r.h = 0.5f * x * x + 1.64493407f - o[0];
-        }
-        return r;
-    }
-    float o[3];
-    if (x <= -1.f) {
-        fd_seriesf<0, 3>(x, expf(x), o);
-    } else if (x < 1.f) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float acc = 0.f;
-            for (int j = FDF_NTAY - 1; j >= 0; --j) acc = fmaf(x, acc, FDF_TAYLOR[k][j]);
-            o[k] = acc;
-        }
-    } else if (x < FD_X0 + FD_NINT * FD_WIDTH) {
-        const int i = (int)((x - FD_X0) / FD_WIDTH);
-        const float a = FD_X0 + FD_WIDTH * i;
-        const float t = (x - a - 0.5f * FD_WIDTH) / (0.5f * FD_WIDTH);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float *c = FDF_CHEB[k][i];
-            float b1 = 0.f, b2 = 0.f;
-            for (int j = FDF_NCHEB - 1; j >= 1; --j) {
-                const float b0 = fmaf(2.f * t, b1, c[j] - b2);
-                b2 = b1;
-                b1 = b0;
-            }
-            o[k] = fmaf(t, b1, c[0] - b2);
-        }
-    } else {
-        const float r2 = 1.f / (x * x), sq = sqrtf(x);
-        const float xp[3] = {sq, x * sq, x * x * sq};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float acc = 0.f;
-            for (int n = FDF_NASYM - 1; n >= 1; --n) acc = fmaf(r2, acc, FDF_ASYM[k][n]);
-            o[k] = xp[k] * FDF_ASYM[k][0] * fmaf(r2, acc, 1.f);
-        }
-    }
-    r.m2 = o[0];
-    r.m1 = o[1];
-    r.h = o[2];
-    return r;
-}
-
 struct FdParamsF {
     float beta, mu_up, mu_dn, ax, ay, az;
     int status;   // as FdParams
@@ -479,41 +524,11 @@ struct FdParamsF {
 template <int D>
 __device__ FdParamsF fd_params_site_f(float n, float Sx, float Sy, float Sz, float eps)
 {
-    constexpr float h = 0.5f * D;
-    constexpr float hl2pi = h * 1.83787707f;   // h log 2 pi
     FdParamsF p;
     const float nS = sqrtf(Sx * Sx + Sy * Sy + Sz * Sz);
-    bool ok = (0.5f * (n - nS) > 0.f) && (eps > 0.f);
-    float t = 0.f, nu1 = 0.f, nu2 = 0.f;
-    if (ok) {
-        const float nup = 0.5f * (n + nS), ndn = 0.5f * (n - nS);
-        const float lA = logf(nup), lB = logf(ndn), lC = logf(n * eps / h);
-        t = logf(h / eps);
-        nu1 = lA - hl2pi + h * t;
-        nu2 = lB - hl2pi + h * t;
-        bool settled = false;
-        for (int it = 0; it < 20 && !settled; ++it) {
-            const Fd3f F1 = fd3f<D>(nu1), F2 = fd3f<D>(nu2);
-            const float sFh = F1.h + F2.h;
-            const float r1 = logf(F1.m1) - h * t + hl2pi - lA;
-            const float r2 = logf(F2.m1) - h * t + hl2pi - lB;
-            const float r3 = logf(sFh) - (h + 1.f) * t + hl2pi - lC;
-            const float ig1 = F1.m1 / F1.m2, ig2 = F2.m1 / F2.m2;
-            const float c1 = F1.m1 / sFh, c2 = F2.m1 / sFh;
-            const float den = -(h + 1.f) + h * (c1 * ig1 + c2 * ig2);
-            float dt = (c1 * ig1 * r1 + c2 * ig2 * r2 - r3) / den;
-            if (!(dt == dt)) break;
-            dt = fmaxf(-1.f, fminf(1.f, dt));
-            const float d1 = fmaxf(-10.f, fminf(10.f, (h * dt - r1) * ig1));
-            const float d2 = fmaxf(-10.f, fminf(10.f, (h * dt - r2) * ig2));
-            t += dt;
-            nu1 += d1;
-            nu2 += d2;
-            settled = fmaxf(fabsf(dt), fmaxf(fabsf(d1), fabsf(d2))) <= 4e-6f * (1.f + fabsf(nu1));
-        }
-        ok = settled;
-    }
-    if (!ok) {   // invalid or unsettled: the double solve decides
+    float t, nu1, nu2;
+    if (!fd_newton_f<D>(0.5f * (n + nS), 0.5f * (n - nS), n, eps, t, nu1, nu2)) {
+        // invalid or unsettled: the double solve decides
         const FdParams q = fd_params_site<D>(n, Sx, Sy, Sz, eps);
         p.beta = (float)q.beta;
         p.mu_up = (float)q.mu_up;
