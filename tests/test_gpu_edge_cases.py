@@ -114,3 +114,17 @@ def test_step_commutes_with_a_global_spin_rotation(q, prec, tol):
     a = out[0].copy()
     a[:, 1:, :] = np.einsum("ij,qjn->qin", R, out[0][:, 1:, :])
     assert rel(out[1], a) < tol
+
+
+def test_lattice_larger_than_the_device_is_an_error(q):
+    # 6e8 D3Q19 sites in FP64 need ~365 GB: the allocation fails, the call
+    # returns QLBM_ERR_OOM, and the device stays usable
+    with pytest.raises(q.QLBMError) as e:
+        q.qlbm_create(3, (1000, 1000, 600), 0.7, 1.0, 1.0, q.QLBM_FP64)
+    assert e.value.code == q.QLBM_ERR_OOM
+    d, dims = 2, (16, 8, 1)
+    st = fields.random_populations(d, dims, seed=4)
+    with q.Lattice(d, dims, 0.7, 1.0, precision="fp64") as lat:
+        lat.set_state(st)
+        lat.step(3)
+        assert np.isfinite(lat.get_state()).all()
