@@ -270,11 +270,15 @@ def bench_ours(args):
         lat.step(NA)
         ev[1].record(stream)
         lat.sync()
+        # an untimed rollout first allocates the checkpoint memory
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        qlbm.qlbm_rollout(lat.h, NA, 0)
         lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
         torch.cuda.synchronize()
         ev[2].record(stream)
         qlbm.qlbm_rollout(lat.h, NA, 0)
         ev[3].record(stream)
+        interval = qlbm.qlbm_rollout_interval(lat.h)
         # observable: total spin magnetisation s_z in the central (L/4)^d box
         lam_T = torch.zeros((b, 4, N), dtype=torch.float64, device="cuda")
         grid = np.zeros(dims[::-1], bool)
@@ -293,15 +297,36 @@ def bench_ours(args):
         t_plain = max_over_ranks(t_plain)
         t_roll = max_over_ranks(t_roll)
         t_adj = max_over_ranks(t_adj)
-        interval = 1
-        while interval * interval < NA:
-            interval += 1
+        # the same with square-root checkpointing forced
+        ksq = 1
+        while ksq * ksq < NA:
+            ksq += 1
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        qlbm.qlbm_rollout(lat.h, NA, ksq)
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        qlbm.qlbm_rollout(lat.h, NA, ksq)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        ev[4].record(stream)
+        dJdtau_sq = qlbm.qlbm_rollout_adjoint(lat.h, lam_T, lam_0)
+        ev[5].record(stream)
+        torch.cuda.synchronize()
+        t_roll_sq = max_over_ranks(ev[2].elapsed_time(ev[3]))
+        t_adj_sq = max_over_ranks(ev[4].elapsed_time(ev[5]))
         adj = {"ratio": round(t_adj / t_plain, 3), "unit": "adjoint sweep time / forward time",
                "forward_ms": round(t_plain, 3), "rollout_ms": round(t_roll, 3),
                "adjoint_ms": round(t_adj, 3), "rollout_overhead": round(t_roll / t_plain, 3),
                "steps": NA, "interval": interval, "precision": "fp32",
                "observable": "sum of s_z over the central box", "dJ_dtau": dJdtau,
-               "note": "adjoint sweep = segment recomputation (two-buffer forward) + reverse steps"}
+               "note": "checkpoint interval chosen by the library (1 = every state kept, written by "
+                       "the forward steps; the sweep recomputes nothing)",
+               "sqrt_checkpoints": {"interval": ksq, "ratio": round(t_adj_sq / t_plain, 3),
+                                    "rollout_overhead": round(t_roll_sq / t_plain, 3),
+                                    "adjoint_ms": round(t_adj_sq, 3),
+                                    "dJ_dtau_matches": dJdtau_sq == dJdtau,
+                                    "note": "segment recomputation (two-buffer forward) + reverse steps"}}
         lat.close()
         del lat, lam_T, lam_0
         torch.cuda.synchronize()

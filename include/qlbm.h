@@ -270,11 +270,17 @@ int qlbm_step_adjoint(qlbm_handle h, const double *lam_next, double *lam, double
 
 /* qlbm_rollout -- nsteps forward steps (as qlbm_step) that also keep, in
  * library-owned device memory, a copy of the state every `interval` steps
- * (0: ceil(sqrt(nsteps)), the square-root checkpointing schedule) for
- * qlbm_rollout_adjoint.  Memory: ceil(nsteps/interval) + interval - 1 state
- * copies; QLBM_ERR_OOM (nothing run) if they do not fit.  A later step,
- * init or set_state discards the record. */
+ * for qlbm_rollout_adjoint.  interval = 1 keeps every state (written by the
+ * forward steps themselves, no extra copies; the reverse sweep recomputes
+ * nothing); interval = 0 chooses: 1 when nsteps states fit in 3/4 of the
+ * device memory available to the handle, else ceil(sqrt(nsteps)), the
+ * square-root checkpointing schedule.  Memory: ceil(nsteps/interval) +
+ * interval - 1 state copies; QLBM_ERR_OOM (nothing run) if they do not fit.
+ * A later step, init or set_state discards the record. */
 int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval);
+
+/* The checkpoint interval the last qlbm_rollout used (-1: none recorded). */
+int64_t qlbm_rollout_interval(qlbm_handle h);
 
 /* qlbm_rollout_adjoint -- reverse sweep over the last qlbm_rollout: for each
  * checkpoint segment, last first, recompute the segment's states from its

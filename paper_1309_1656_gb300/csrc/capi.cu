@@ -479,16 +479,26 @@ int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval)
     if (h->eq_path != QLBM_EQ_DIRECT)
         return fail(h, QLBM_ERR_UNSUPPORTED, "qlbm_rollout: the reverse mode covers the direct equilibrium path");
     if (!h->ops->adjoint) return fail(h, QLBM_ERR_UNSUPPORTED, "qlbm_rollout: no reverse mode for this precision");
+    const size_t sb = h->state_bytes();
     int64_t K = interval;
     if (K == 0) {
-        K = 1;
-        while (K * K < nsteps) ++K;
+        // automatic: keep every state when they fit in 3/4 of the device
+        // memory available to the handle (no recomputation in the reverse
+        // sweep), else square-root checkpointing
+        size_t free_b = 0, total_b = 0;
+        CK(h, cudaMemGetInfo(&free_b, &total_b));
+        const double avail = (double)free_b + (double)(h->ck_slots + h->seg_slots) * (double)sb;
+        if ((double)nsteps * (double)sb <= 0.75 * avail) {
+            K = 1;
+        } else {
+            K = 1;
+            while (K * K < nsteps) ++K;
+        }
     }
     const int64_t nseg = (nsteps + K - 1) / K;
     const int64_t need_seg = K > 1 ? K - 1 : 0;
     if (h->ck_slots < nseg || h->seg_slots < need_seg) {
         free_rollout(h);
-        const size_t sb = h->state_bytes();
         if (nseg > 0) {
             cudaError_t e = cudaMalloc(&h->ck, sb * (size_t)nseg);
             if (e == cudaSuccess && need_seg > 0) e = cudaMalloc(&h->seg, sb * (size_t)need_seg);
@@ -504,17 +514,30 @@ int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval)
         h->ck_slots = nseg;
         h->seg_slots = need_seg;
     }
-    const size_t sb = h->state_bytes();
-    for (int64_t i = 0; i < nsteps; ++i) {
-        if (i % K == 0) CK(h, h->ops->copy_natural(h, static_cast<char *>(h->ck) + sb * (size_t)(i / K)));
-        CK(h, h->ops->step(h, h->parity == 1));
-        h->parity ^= 1;
-        h->t += 1;
+    if (K == 1 && nsteps > 0) {
+        // every state kept: the two-buffer kernel writes step i's result
+        // straight into slot i + 1 (the same bytes as an in-place step), and
+        // the last step back into the live buffer in natural order
+        char *ck = static_cast<char *>(h->ck);
+        CK(h, h->ops->copy_natural(h, ck));
+        for (int64_t i = 0; i + 1 < nsteps; ++i) CK(h, h->ops->push(h, ck + sb * (size_t)i, ck + sb * (size_t)(i + 1)));
+        CK(h, h->ops->push(h, ck + sb * (size_t)(nsteps - 1), h->pop));
+        h->parity = 0;
+        h->t += nsteps;
+    } else {
+        for (int64_t i = 0; i < nsteps; ++i) {
+            if (i % K == 0) CK(h, h->ops->copy_natural(h, static_cast<char *>(h->ck) + sb * (size_t)(i / K)));
+            CK(h, h->ops->step(h, h->parity == 1));
+            h->parity ^= 1;
+            h->t += 1;
+        }
     }
     h->ro_steps = nsteps;
     h->ro_interval = K;
     return QLBM_OK;
 }
+
+int64_t qlbm_rollout_interval(qlbm_handle h) { return (h && h->ro_steps >= 0) ? h->ro_interval : -1; }
 
 int qlbm_rollout_adjoint(qlbm_handle h, const double *lam_T, double *lam_0, double *dJ_dtau, int ptr_kind)
 {

@@ -71,6 +71,7 @@ _set_state = _sig("qlbm_set_state", _i, [_vp, _vp, _i])
 _step_adjoint = _sig("qlbm_step_adjoint", _i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i])
 _rollout = _sig("qlbm_rollout", _i, [_vp, _i64, _i64])
 _rollout_adjoint = _sig("qlbm_rollout_adjoint", _i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i])
+_rollout_interval = _sig("qlbm_rollout_interval", _i64, [_vp])
 _init_adjoint = _sig("qlbm_init_equilibrium_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i])
 _fd_params = _sig("qlbm_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64), _i])
 _fd_params_adjoint = _sig("qlbm_fd_params_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
@@ -209,6 +210,10 @@ def qlbm_step_adjoint(h, lam_next, lam):
 
 def qlbm_rollout(h, nsteps, interval=0):
     _check(_rollout(h, int(nsteps), int(interval)), h)
+
+
+def qlbm_rollout_interval(h):
+    return _rollout_interval(h)
 
 
 def qlbm_rollout_adjoint(h, lam_T, lam_0):

@@ -77,10 +77,17 @@ def test_checkpoint_interval_does_not_change_the_result(q, prec):
     fl = fields.random_fields(d, dims, seed=9)
     lam_T = np.random.default_rng(8).normal(size=(19, 4, int(np.prod(dims))))
     res = []
-    for interval in (1, 2, 5, 13):
+    with q.Lattice(d, dims, 0.7, 1.0, precision=prec) as lat:
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        lat.step(13)
+        plain_end = lat.get_state()
+    for interval in (0, 1, 2, 5, 13):
         with q.Lattice(d, dims, 0.7, 1.0, precision=prec) as lat:
             lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
             lat.rollout(13, interval)
+            # a small rollout keeps every state automatically
+            assert q.qlbm_rollout_interval(lat.h) == (interval or 1)
+            assert np.array_equal(lat.get_state(), plain_end)
             res.append(lat.rollout_adjoint(lam_T))
     for lam, g in res[1:]:
         assert np.array_equal(lam, res[0][0])
