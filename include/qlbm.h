@@ -273,8 +273,8 @@ int qlbm_step_adjoint(qlbm_handle h, const double *lam_next, double *lam, double
  * for qlbm_rollout_adjoint.  interval = 1 keeps every state (written by the
  * forward steps themselves, no extra copies; the reverse sweep recomputes
  * nothing); interval = 0 chooses: 1 when nsteps states fit in 3/4 of the
- * device memory available to the handle, else ceil(sqrt(nsteps)), the
- * square-root checkpointing schedule.  Memory: ceil(nsteps/interval) +
+ * device memory available to the handle (and their allocation succeeds),
+ * else ceil(sqrt(nsteps)), the square-root checkpointing schedule.  Memory: ceil(nsteps/interval) +
  * interval - 1 state copies; QLBM_ERR_OOM (nothing run) if they do not fit.
  * A later step, init or set_state discards the record. */
 int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval);

@@ -495,13 +495,24 @@ int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval)
             while (K * K < nsteps) ++K;
         }
     }
-    const int64_t nseg = (nsteps + K - 1) / K;
-    const int64_t need_seg = K > 1 ? K - 1 : 0;
+    int64_t nseg = (nsteps + K - 1) / K;
+    int64_t need_seg = K > 1 ? K - 1 : 0;
     if (h->ck_slots < nseg || h->seg_slots < need_seg) {
         free_rollout(h);
         if (nseg > 0) {
             cudaError_t e = cudaMalloc(&h->ck, sb * (size_t)nseg);
             if (e == cudaSuccess && need_seg > 0) e = cudaMalloc(&h->seg, sb * (size_t)need_seg);
+            if (e != cudaSuccess && interval == 0 && K == 1 && nsteps > 1) {
+                // the automatic choice did not fit after all: square-root checkpoints
+                cudaGetLastError();
+                free_rollout(h);
+                K = 1;
+                while (K * K < nsteps) ++K;
+                nseg = (nsteps + K - 1) / K;
+                need_seg = K - 1;
+                e = cudaMalloc(&h->ck, sb * (size_t)nseg);
+                if (e == cudaSuccess && need_seg > 0) e = cudaMalloc(&h->seg, sb * (size_t)need_seg);
+            }
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 free_rollout(h);
