@@ -460,6 +460,12 @@ def bench_ours(args):
             "traffic": None if traffic is None else round(traffic * N),
             "algorithmic_bytes_per_launch": r32["alg_bytes"],
             "kernel": "k_step_aa<%d,%s>" % (d, prim)}
+    if traffic is not None:
+        # DRAM bytes actually moved per launch (ncu) over the same event time:
+        # below the algorithmic bytes by the writes still in L2 at kernel end
+        dram = traffic * N / (r32["step_ms"] * 1e-3) / 1e9
+        roof["dram_achieved"] = round(dram, 1)
+        roof["dram_frac"] = round(dram / peak, 4)
     line = {
         "metric": METRIC, "value": round(r32["mlups"], 1), "unit": "MLUPS", "n_gpus": ws,
         "steps": K, "warmup": W, "ms_per_step": round(r32["total_ms"] / K, 5),
