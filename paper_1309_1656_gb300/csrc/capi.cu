@@ -256,6 +256,7 @@ int qlbm_create(qlbm_handle *out, int lattice, const int64_t dims[3], double tau
     h->elem_bytes = (precision == QLBM_FP64 || precision == QLBM_DF64) ? 8 : (precision == QLBM_FP32 ? 4 : 2);
 
     cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     size_t bytes = (size_t)h->b * 4 * (size_t)g.P * h->elem_bytes;
     if (e == cudaSuccess) e = cudaMalloc(&h->pop, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->flags, sizeof(unsigned));

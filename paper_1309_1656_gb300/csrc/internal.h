@@ -37,6 +37,7 @@ struct qlbm_ctx {
     qlbm::HostConsts hc{};
     cudaStream_t stream = nullptr;
     int device = 0;
+    int sms = 0;                    // streaming multiprocessors of the device
     void *pop = nullptr;            // b*4*P elements of the storage type
     size_t elem_bytes = 0;
     int parity = 0;                 // 1: last written by an even step (swapped)
@@ -144,6 +145,24 @@ inline dim3 site_block(const Grid &g) { return dim3(site_block_width(g.nx)); }
 inline dim3 site_grid(const Grid &g, int bx)
 {
     return dim3((unsigned)((int64_t)g.nxb * g.ny * g.nz));
+}
+
+// Rows per block of the row-pipelined step (k_step_aa_rows): rmax, or fewer
+// where the grid would otherwise fall below four waves of resident blocks
+// (the idle SMs of a short grid's last wave cost more than the pipelining
+// gains).
+inline int step_rows_per_block(const Grid &g, int rmax, int resident_per_sm, int sms)
+{
+    const int64_t blocks = (int64_t)g.nxb * g.ny * g.nz;
+    const int64_t wave = (int64_t)resident_per_sm * (sms > 0 ? sms : 1);
+    int64_t r = blocks / (4 * wave);
+    if (r > rmax) r = rmax;
+    return r < 1 ? 1 : (int)r;
+}
+inline dim3 row_group_grid(const Grid &g, int rpb)
+{
+    const int64_t rows = (int64_t)g.ny * g.nz;
+    return dim3((unsigned)((int64_t)g.nxb * ((rows + rpb - 1) / rpb)));
 }
 
 }  // namespace qlbm

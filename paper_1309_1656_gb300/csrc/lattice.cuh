@@ -412,9 +412,9 @@ struct CodecF16Dev {
     __device__ __forceinline__ S store(R v) const { return __float2half_rn(v); }
     // pairs convert in one instruction each way (half2 <-> float2); the
     // rounding is the same round-to-nearest as __float2half_rn per value
-    __device__ __forceinline__ void load4(const V *p, R &f, R &x, R &y, R &z) const
+    __device__ __forceinline__ void load4(const V *p, R &f, R &x, R &y, R &z) const { decode4(*p, f, x, y, z); }
+    __device__ __forceinline__ void decode4(const V &v, R &f, R &x, R &y, R &z) const
     {
-        const uint2 v = *p;
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
         f = a.x;

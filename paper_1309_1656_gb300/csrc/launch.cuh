@@ -114,6 +114,23 @@ template <int D, class Codec> struct Launchers {
                 else
                     k_step_aa_df2<D, false, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
             }
+        } else if constexpr (RowPipelined<Codec>::value) {
+            // rows per block from a sweep on GB300 (FP16): D2Q9 4096^2 gains
+            // 14 % at 8, D3Q19 192^3 - 256^3 4-7 % at 4 (more rows lose to the tail)
+            const int rpb = step_rows_per_block(h->g, D == 2 ? 8 : 4, step_min_blocks<D, Codec>(), h->sms);
+            const dim3 grr = row_group_grid(h->g, rpb);
+            const size_t sm = rows_smem_bytes<D, Codec>((int)blk.x);
+            if (h->mag) {
+                if (odd)
+                    k_step_aa_rows<D, Codec, true, true><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
+                else
+                    k_step_aa_rows<D, Codec, false, true><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
+            } else {
+                if (odd)
+                    k_step_aa_rows<D, Codec, true><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
+                else
+                    k_step_aa_rows<D, Codec, false><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
+            }
         } else if (h->mag) {
             if (odd)
                 k_step_aa<D, Codec, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);

@@ -115,4 +115,117 @@ k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typena
     if (flag) atomicOr(flags, flag);
 }
 
+// Codecs whose step runs row-pipelined (k_step_aa_rows): those whose b
+// vectors per site fit twice in shared memory at the step's occupancy
+// (FP16: 8 bytes per vector).
+template <class Codec> struct RowPipelined {
+    static constexpr bool value = false;
+};
+template <> struct RowPipelined<CodecF16Dev> {
+    static constexpr bool value = true;
+};
+
+__device__ __forceinline__ SiteIdx site_at(const Grid &g, int x, int row)
+{
+    SiteIdx si;
+    si.x = x;
+    si.y = row % g.ny;
+    si.z = row / g.ny;
+    si.s = row * g.nx + x;
+    return si;
+}
+
+// Asynchronous global -> shared copy of one 8- or 16-byte vector
+// (cp.async, completion tracked per thread by commit / wait groups).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_vec(void *dst, const void *src)
+{
+    static_assert(BYTES == 8 || BYTES == 16, "cp.async copies 4, 8 or 16 bytes");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %1;\n\t"
+                 "cp.async.ca.shared.global [%0], [g], %2;\n\t}\n" ::"r"(d),
+                 "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Starts the copies of the b stored vectors of site si (the slots an even
+// step reads at x, or an odd step reads at x + e_q) into dst[q * stride].
+template <int D, class Codec, bool SWAPPED>
+__device__ __forceinline__ void fetch_site(const Planes<typename Codec::S, Lattice<D>::Q> &pl,
+                                           const Grid &g, const SiteIdx &si,
+                                           typename QuadOf<typename Codec::S>::V *dst, int stride)
+{
+    using V = typename QuadOf<typename Codec::S>::V;
+#pragma unroll
+    for (int q = 0; q < Lattice<D>::Q; ++q) {
+        const int s = SWAPPED ? neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q)) : si.s;
+        cp_async_vec<sizeof(V)>(dst + q * stride, pl.p[q] + s);
+    }
+}
+
+// Dynamic shared memory of k_step_aa_rows: two stages of b vectors per
+// thread.
+template <int D, class Codec> constexpr size_t rows_smem_bytes(int block)
+{
+    return 2 * (size_t)Lattice<D>::Q * block * sizeof(typename QuadOf<typename Codec::S>::V);
+}
+
+// The same AA step as k_step_aa, row-pipelined: block (chunk c, group r)
+// updates the sites of x-chunk c in the rpb consecutive rows
+// r*rpb .. r*rpb + rpb - 1.  Each thread copies its next row's vectors into
+// shared memory (cp.async) before it works on the current row, so that one
+// row's loads are in flight while the previous row computes, without
+// holding them in registers; a thread reads back only what it copied, so no
+// block barrier is needed.  Each location is read and written by exactly
+// one site update per step, so the early loads of row r + 1 never meet the
+// stores of row r.
+template <int D, class Codec, bool ODD, bool MAG = false>
+__global__ void __launch_bounds__(kStepBlock, step_min_blocks<D, Codec>())
+k_step_aa_rows(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typename Codec::R> k,
+               Codec codec, int rpb, unsigned *__restrict__ flags)
+{
+    using R = typename Codec::R;
+    using V = typename QuadOf<typename Codec::S>::V;
+    constexpr int Q = Lattice<D>::Q;
+    extern __shared__ __align__(16) unsigned char rows_smem[];
+    const int bw = blockDim.x;
+    // stage t, slot q of this thread at mine[(t * Q + q) * bw]
+    V *mine = reinterpret_cast<V *>(rows_smem) + threadIdx.x;
+    const int grp = blockIdx.x / g.nxb;
+    const int x = (blockIdx.x - grp * g.nxb) * bw + threadIdx.x;
+    if (x >= g.nx) return;
+    const int row0 = grp * rpb;
+    const int rend = min(row0 + rpb, g.ny * g.nz);
+    fetch_site<D, Codec, ODD>(pl, g, site_at(g, x, row0), mine, bw);
+    cp_async_commit();
+    unsigned flag = 0;
+    for (int row = row0, t = 0; row < rend; ++row, t ^= 1) {
+        if (row + 1 < rend) fetch_site<D, Codec, ODD>(pl, g, site_at(g, x, row + 1), mine + (t ^ 1) * Q * bw, bw);
+        cp_async_commit();
+        cp_async_wait<1>();     // this row's copies have landed
+        R f[Q], sx[Q], sy[Q], sz[Q];
+        const V *cur = mine + t * Q * bw;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int p = ODD ? opposite<D>(q) : q;     // population held by slot q
+            codec.decode4(cur[q * bw], f[p], sx[p], sy[p], sz[p]);
+        }
+        flag |= Codec::template collide<D>(f, sx, sy, sz, k);
+        if constexpr (MAG) rotate_spins<D, R>(sx, sy, sz, k.rot);
+        // store addresses recomputed from g.zero (see k_step_aa)
+        const SiteIdx so = site_at(g, x + g.zero, row);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int slot = ODD ? q : opposite<D>(q);
+            const int s = ODD ? neighbour(g, so, cx<D>(q), cy<D>(q), cz<D>(q)) : so.s;
+            codec.store4(pl.p[slot] + s, f[q], sx[q], sy[q], sz[q]);
+        }
+    }
+    if (flag) atomicOr(flags, flag);
+}
+
 }  // namespace qlbm
