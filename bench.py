@@ -15,6 +15,7 @@ ends with the FP64 conservation reduction.  Reported:
   fp64        the same for FP64 storage
   df64        the same for double-float storage (two floats per value,
               double-float arithmetic on the FP32 pipes)
+  fp64df      the same for FP64 storage stepped in double-float arithmetic
   e2e         MLUPS through the C ABI with host buffers: init from pinned
               host fields, K steps, moments back to pinned host memory
   adjoint     reverse sweep time (segment recomputation + adjoint steps) /
@@ -57,7 +58,7 @@ WORKLOADS = {
 
 
 def bytes_per_value(prec):
-    return {"fp64": 8, "df64": 8, "fp32": 4, "fp16dev": 2}[prec]
+    return {"fp64": 8, "df64": 8, "fp64df": 8, "fp32": 4, "fp16dev": 2}[prec]
 
 
 def make_fields(w):
@@ -435,14 +436,14 @@ def bench_ours(args):
         (normwise, max |x - x_ref| / max |x_ref|)."""
         err = lambda a, b_: float(np.max(np.abs(a - b_)) / np.max(np.abs(b_)))
         res = {"steps": nsteps, "norm": "max |x - x_oracle| / max |x_oracle|"}
-        for prec in ("fp64", "df64", "fp32", "fp16dev"):
+        for prec in ("fp64", "fp64df", "df64", "fp32", "fp16dev"):
             with qlbm.Lattice(d, sdims, w["tau"], w["beta0"], precision=prec) as lat:
                 lat.init_equilibrium(sfl["rho4"], sfl["u"], sfl["eps"])
                 lat.step(nsteps)
                 r4, uu, ee = lat.moments()
                 e = {"n": err(r4[0], mom_ref[0][0]), "S": err(r4[1:], mom_ref[0][1:]),
                      "u": err(uu, mom_ref[1]), "eps": err(ee, mom_ref[2])}
-                if prec in ("fp64", "df64"):
+                if prec in ("fp64", "fp64df", "df64"):
                     e["state"] = err(lat.get_state(), st_ref)
                     e["state_per_step"] = e["state"] / nsteps
                 res[prec] = {k: float("%.3g" % v) for k, v in e.items()}
@@ -470,7 +471,8 @@ def bench_ours(args):
         "metric": METRIC, "value": round(r32["mlups"], 1), "unit": "MLUPS", "n_gpus": ws,
         "steps": K, "warmup": W, "ms_per_step": round(r32["total_ms"] / K, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32", "df64": "f32x2"}[prim],
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32", "df64": "f32x2",
+                  "fp64df": "f64-storage/f32x2"}[prim],
         "data": "synthetic",
         "config": {"workload": w["desc"], "lattice": "D3Q19" if d == 3 else "D2Q9",
                    "dims": list(dims), "sites": N, "tau": w["tau"], "beta0": w["beta0"],
@@ -627,7 +629,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="d3q19-128", choices=sorted(WORKLOADS))
-    ap.add_argument("--precisions", default="fp32,fp64,df64")
+    ap.add_argument("--precisions", default="fp32,fp64,fp64df,df64")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -72,12 +72,18 @@ typedef enum qlbm_lattice { QLBM_D2Q9 = 2, QLBM_D3Q19 = 3 } qlbm_lattice;
    floats (8 bytes, 48-bit significand) and computes in double-float
    arithmetic on the single-precision pipes (results within ~1e-14 of double
    per step; no reverse mode: the adjoint calls return
-   QLBM_ERR_UNSUPPORTED). */
+   QLBM_ERR_UNSUPPORTED).  QLBM_FP64_DF stores IEEE doubles exactly as
+   QLBM_FP64 does (same layout, same exact state read-out and set-up, same
+   moments, reductions and Fermi-Dirac kernels) but steps in double-float
+   arithmetic: each double is split into two floats, the step runs on the
+   single-precision pipes and rounds its result to double (within ~1e-14 of
+   the QLBM_FP64 step per step; no reverse mode). */
 typedef enum qlbm_precision {
     QLBM_FP64 = 0,
     QLBM_FP32 = 1,
     QLBM_FP16_DEV = 2,
-    QLBM_DF64 = 3
+    QLBM_DF64 = 3,
+    QLBM_FP64_DF = 4
 } qlbm_precision;
 
 typedef enum qlbm_ptr_kind { QLBM_HOST = 0, QLBM_DEVICE = 1 } qlbm_ptr_kind;
@@ -243,7 +249,8 @@ int qlbm_fd_params_adjoint(qlbm_handle h, const double *g_beta, const double *g_
  * with U, beta, mu_s recovered per site as in qlbm_fd_params and
  * n_s = (2 pi/beta)^(d/2) F_{d/2-1}(beta mu_s); it agrees with the direct path
  * to the accuracy of the solve, and sites without a solution keep rho.
- * QLBM_FP64 handles only (QLBM_ERR_UNSUPPORTED otherwise); forward stepping
+ * QLBM_FP64 and QLBM_FP64_DF handles only (QLBM_ERR_UNSUPPORTED otherwise;
+ * both step this path in double); forward stepping
  * only (qlbm_rollout returns QLBM_ERR_UNSUPPORTED on this path). */
 #define QLBM_EQ_DIRECT 0
 #define QLBM_EQ_FD_PARAMS 1

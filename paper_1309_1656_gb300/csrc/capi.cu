@@ -217,7 +217,8 @@ int qlbm_create(qlbm_handle *out, int lattice, const int64_t dims[3], double tau
     if (!out || !dims) return fail(nullptr, QLBM_ERR_INVALID_ARG, "null argument");
     if (lattice != QLBM_D2Q9 && lattice != QLBM_D3Q19)
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "lattice must be QLBM_D2Q9 or QLBM_D3Q19");
-    if (precision != QLBM_FP64 && precision != QLBM_FP32 && precision != QLBM_FP16_DEV && precision != QLBM_DF64)
+    if (precision != QLBM_FP64 && precision != QLBM_FP32 && precision != QLBM_FP16_DEV && precision != QLBM_DF64 &&
+        precision != QLBM_FP64_DF)
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "unknown precision");
     if (!(tau > 0.0) || !(beta0 > 0.0) || !(dt > 0.0))
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "tau, beta0 and dt must be > 0");
@@ -253,7 +254,8 @@ int qlbm_create(qlbm_handle *out, int lattice, const int64_t dims[3], double tau
         delete h;
         return fail(nullptr, QLBM_ERR_INVALID_ARG, "lattice too large: at most 2^31 - 64 sites");
     }
-    h->elem_bytes = (precision == QLBM_FP64 || precision == QLBM_DF64) ? 8 : (precision == QLBM_FP32 ? 4 : 2);
+    h->elem_bytes =
+        (precision == QLBM_FP64 || precision == QLBM_DF64 || precision == QLBM_FP64_DF) ? 8 : (precision == QLBM_FP32 ? 4 : 2);
 
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -673,7 +675,7 @@ int qlbm_set_equilibrium_path(qlbm_handle h, int path)
     if (path != QLBM_EQ_DIRECT && path != QLBM_EQ_FD_PARAMS)
         return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_equilibrium_path: unknown path");
     if (path == QLBM_EQ_FD_PARAMS && !h->ops->step_fd)
-        return fail(h, QLBM_ERR_UNSUPPORTED, "the Fermi-Dirac equilibrium path needs QLBM_FP64 storage");
+        return fail(h, QLBM_ERR_UNSUPPORTED, "the Fermi-Dirac equilibrium path needs FP64 storage (QLBM_FP64 or QLBM_FP64_DF)");
     h->eq_path = path;
     h->ro_steps = -1;
     return QLBM_OK;

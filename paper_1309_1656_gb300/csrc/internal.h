@@ -106,6 +106,10 @@ const LatticeOps *ops_d3q19_fp64();
 const LatticeOps *ops_d3q19_fp32();
 const LatticeOps *ops_d3q19_fp16();
 const LatticeOps *ops_d3q19_df64();
+const LatticeOps *ops_d2q9_fp64df();
+const LatticeOps *ops_d3q19_fp64df();
+// the double-float step on FP64 storage (kernels_<lattice>_fp64df.cu)
+template <int D> cudaError_t step_f64df(qlbm_ctx *h, bool odd);
 
 inline const LatticeOps *lattice_ops(int d, int prec)
 {
@@ -114,6 +118,7 @@ inline const LatticeOps *lattice_ops(int d, int prec)
     case QLBM_FP32: return d == 2 ? ops_d2q9_fp32() : ops_d3q19_fp32();
     case QLBM_FP16_DEV: return d == 2 ? ops_d2q9_fp16() : ops_d3q19_fp16();
     case QLBM_DF64: return d == 2 ? ops_d2q9_df64() : ops_d3q19_df64();
+    case QLBM_FP64_DF: return d == 2 ? ops_d2q9_fp64df() : ops_d3q19_fp64df();
     default: return nullptr;
     }
 }

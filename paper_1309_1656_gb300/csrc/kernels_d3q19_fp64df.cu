@@ -1,0 +1,25 @@
+// D3Q19 (Sec. 3.1, d = 3, b = 19) step for FP64 storage in double-float arithmetic
+// (QLBM_FP64_DF); the other operations of that precision are the FP64 ones
+// (kernels_d3q19_fp64.cu holds its dispatch table).
+#include "f64df.cuh"
+#include "launch.cuh"
+
+namespace qlbm {
+
+template <int D> cudaError_t step_f64df(qlbm_ctx *h, bool odd)
+{
+    const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+    const Planes<double, Lattice<D>::Q> pl = Launchers<D, CodecF64>::planes(h);
+    const Coll<df> k = make_coll<df>(h);
+    if (h->mag) {
+        if (odd) k_step_aa_f64df<D, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, h->flags);
+        else k_step_aa_f64df<D, false, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, h->flags);
+    } else {
+        if (odd) k_step_aa_f64df<D, true, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, h->flags);
+        else k_step_aa_f64df<D, false, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, h->flags);
+    }
+    return cudaGetLastError();
+}
+template cudaError_t step_f64df<3>(qlbm_ctx *h, bool odd);
+
+}  // namespace qlbm

@@ -31,12 +31,14 @@ QLBM_FP64 = 0
 QLBM_FP32 = 1
 QLBM_FP16_DEV = 2
 QLBM_DF64 = 3
+QLBM_FP64_DF = 4
 QLBM_HOST = 0
 QLBM_DEVICE = 1
 QLBM_EQ_DIRECT = 0
 QLBM_EQ_FD_PARAMS = 1
 
-PRECISIONS = {"fp64": QLBM_FP64, "fp32": QLBM_FP32, "fp16dev": QLBM_FP16_DEV, "df64": QLBM_DF64}
+PRECISIONS = {"fp64": QLBM_FP64, "fp32": QLBM_FP32, "fp16dev": QLBM_FP16_DEV, "df64": QLBM_DF64,
+              "fp64df": QLBM_FP64_DF}
 
 LIB_PATH = _build.LIB
 if not os.path.exists(LIB_PATH):

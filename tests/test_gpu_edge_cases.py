@@ -9,7 +9,7 @@ from paper_1309_1656_gb300 import fields
 
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp64", "df64", "fp32", "fp16dev"]
+PRECS = ["fp64", "df64", "fp64df", "fp32", "fp16dev"]
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +37,7 @@ def test_zero_steps_leave_the_state(q, prec):
         assert np.array_equal(lat.get_state(), before)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("df64", 1e-12)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("df64", 1e-12), ("fp64df", 1e-12)])
 @pytest.mark.parametrize("d,dims", [(2, (1, 1, 1)), (2, (1, 7, 1)), (2, (5, 1, 1)),
                                     (3, (1, 1, 1)), (3, (3, 1, 2)), (3, (1, 4, 1))])
 def test_lattices_one_site_wide_vs_oracle(q, oracle_mod, prec, tol, d, dims):
@@ -54,7 +54,7 @@ def test_lattices_one_site_wide_vs_oracle(q, oracle_mod, prec, tol, d, dims):
 @pytest.mark.parametrize("d,dims", [(2, (37, 29, 1)), (3, (12, 9, 7))])
 def test_pure_density_stays_spinless(q, oracle_mod, prec, d, dims):
     # W_i ~ 1: every spin component is zero and stays exactly zero; the
-    # densities follow the oracle (FP64 / DF64) or the FP32 moment bound
+    # densities follow the oracle (the 64-bit precisions)
     fl = fields.random_fields(d, dims, seed=8)
     fl["rho4"][1:] = 0.0
     with q.Lattice(d, dims, 0.8, 1.0, precision=prec) as lat:
@@ -62,7 +62,7 @@ def test_pure_density_stays_spinless(q, oracle_mod, prec, d, dims):
         lat.step(50)
         st = lat.get_state()
     assert np.all(st[:, 1:, :] == 0.0)
-    if prec in ("fp64", "df64"):
+    if prec in ("fp64", "df64", "fp64df"):
         ref = oracle_mod.init_equilibrium(d, dims, 1.0, fl["rho4"], fl["u"], fl["eps"])
         ref = oracle_mod.run(d, dims, 0.8, 1.0, 50, ref)
         assert rel(st, ref) < 50 * 1e-12
@@ -71,7 +71,7 @@ def test_pure_density_stays_spinless(q, oracle_mod, prec, d, dims):
 @pytest.mark.parametrize("prec", PRECS)
 def test_uniform_equilibrium_is_a_fixed_point(q, oracle_mod, prec):
     # n = 1, S = 0, u = 0, eps = eps0: the deviation codecs hold exact zeros
-    # and keep them; the plain codecs keep w_i up to rounding
+    # and keep them; the 64-bit precisions keep w_i up to rounding
     d, dims = 3, (8, 6, 5)
     N = int(np.prod(dims))
     rho4 = np.zeros((4, N))
@@ -94,7 +94,7 @@ def rotation(axis, angle):
     return np.eye(3) + np.sin(angle) * K + (1 - np.cos(angle)) * K @ K
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("df64", 1e-12), ("fp32", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("df64", 1e-12), ("fp64df", 1e-12), ("fp32", 1e-6)])
 def test_step_commutes_with_a_global_spin_rotation(q, prec, tol):
     # W -> V W V* for a fixed V in SU(2) rotates every Bloch vector by the
     # same R in SO(3); the collision and streaming act on s linearly with
