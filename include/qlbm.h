@@ -264,7 +264,8 @@ int qlbm_set_equilibrium_path(qlbm_handle h, int path);
  * TransportStep) is differentiated exactly by the chain rule; streaming is a
  * permutation, so its adjoint pulls lambda_i(x + e_i).  dJ/dtau follows from
  * omega = dt/tau in Eq. CollisionStep.  Single-precision handles carry the
- * cotangents in float internally.
+ * cotangents in float internally.  QLBM_DF64 and QLBM_FP64_DF handles have
+ * no reverse mode: these calls return QLBM_ERR_UNSUPPORTED.
  * ---------------------------------------------------------------------- */
 
 /* qlbm_step_adjoint -- one reverse step at the handle's current state W^n:
