@@ -59,3 +59,41 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
                              args["precision"])
         assert e.value.code == qlbm.QLBM_ERR_INVALID_ARG
         assert qlbm.qlbm_last_error(None)
+
+
+def header_constants():
+    """Enumerators and #define constants of include/*.h: name -> value."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(QLBM_[A-Z0-9_]+)\s*=\s*(-?\d+)", text):
+            out[m.group(1)] = int(m.group(2))
+        for m in re.finditer(r"#define\s+(QLBM_[A-Z0-9_]+)\s+(-?\d+)\b", text):
+            out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def test_binding_constants_match_the_header():
+    from paper_1309_1656_gb300 import qlbm
+    consts = header_constants()
+    for name in ("QLBM_FP64", "QLBM_FP32", "QLBM_FP16_DEV", "QLBM_DF64", "QLBM_FP64_DF",
+                 "QLBM_ERR_OOM", "QLBM_ERR_INVALID_ARG", "QLBM_ERR_UNSUPPORTED"):
+        assert name in consts, name
+    checked = 0
+    for name, value in consts.items():
+        if hasattr(qlbm, name):
+            assert getattr(qlbm, name) == value, name
+            checked += 1
+    assert checked >= 10
+    # every precision the binding names is one the header declares
+    precs = {v for k, v in consts.items() if k in ("QLBM_FP64", "QLBM_FP32", "QLBM_FP16_DEV", "QLBM_DF64",
+                                                    "QLBM_FP64_DF")}
+    assert set(qlbm.PRECISIONS.values()) == precs
+
+
+def test_create_rejects_the_precision_after_the_last(lib):
+    from paper_1309_1656_gb300 import qlbm
+    bad = max(qlbm.PRECISIONS.values()) + 1
+    with pytest.raises(qlbm.QLBMError) as e:
+        qlbm.qlbm_create(2, (4, 4, 1), 0.8, 1.0, 1.0, bad)
+    assert e.value.code == qlbm.QLBM_ERR_INVALID_ARG
