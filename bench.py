@@ -496,6 +496,9 @@ def bench_ours(args):
         if p_ == "fp64":
             # bound by FP64 issue: 2 FP64 lanes/clk/SM x 152 SMs x clock
             line[p_]["bound"] = "alu (fp64 pipe, see profiles/k_step_aa_d3q19_fp64_128.md)"
+        if p_ == "fp64df":
+            line[p_]["bound"] = ("alu (fp64 pipe: moment sums and rounding; integer pipe: splits; see "
+                                 "profiles/k_step_aa_f64df_d3q19_fp64df_128.md)")
     if growth:
         line["error_growth"] = growth
     if clocks:
