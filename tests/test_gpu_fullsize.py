@@ -114,7 +114,7 @@ def storage_tol(oracle_mod, d, beta0, exp, prec):
     return 2.0 * ((b + 2) * ua + us) * np.max(np.abs(dev)) / np.max(np.abs(exp))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp64df", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64df", "fp32", "fp16dev"])
 def test_d3q19_128_bench_configuration(q, oracle_mod, prec):
     d, dims, tau, beta0 = 3, (128, 128, 128), 0.7, 1.0
     fl = fields.modes(3, dims, seed=2)
