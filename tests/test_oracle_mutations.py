@@ -60,6 +60,16 @@ MUTATIONS = {
         ("out[4] = 2.0 * cimag(conj(v0) * v1);", "out[4] = -2.0 * cimag(conj(v0) * v1);"),
     "field: rotation of the wrong sense":
         ("U->m[0][0] = c - I * s * bz;", "U->m[0][0] = c + I * s * bz;"),
+    "global energy without the 1/2 (Eq. GlobalTotalEnergy)":
+        ("en += 0.5 * e2 * t;", "en += e2 * t;"),
+    "global momentum without the lattice constant xi (Eq. GlobalVelocity)":
+        ("double e = L.xi * L.idx[i][k];\n                mom[k] += e * t;",
+         "double e = L.idx[i][k];\n                mom[k] += e * t;"),
+    "velocity not divided by the density (Eq. DiscrAvr)":
+        ("M->u[k] = (k < L->d) ? acc / M->n : 0.0;", "M->u[k] = (k < L->d) ? acc : 0.0;"),
+    "adjoint read-out: sign of the s_y cotangent":
+        ("o[2 * N] = 0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));",
+         "o[2 * N] = -0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));"),
 }
 
 

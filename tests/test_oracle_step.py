@@ -5,7 +5,8 @@
 * dt/tau = 1 replaces every population by the streamed local equilibrium;
 * global density matrix, momentum and total energy are conserved
   (Eqs. GlobalDensity, GlobalVelocity, GlobalTotalEnergy), and the collision
-  conserves them site by site;
+  conserves them site by site; on an equilibrium state they equal the site
+  means of rho, n u and n (eps + |u|^2/2) formed from the input fields;
 * a homogeneous equilibrium is a fixed point; a homogeneous non-equilibrium
   state relaxes as (1 - dt/tau)^n exactly (streaming is the identity there);
 * Hermiticity is preserved exactly; the step commutes with a global SU(2)
@@ -100,6 +101,25 @@ def test_global_conservation(oracle_mod, d, dims):
     assert np.max(np.abs(c1 - c0)) < 1e-14 * scale * 10
     # the state did change
     assert rel(st2, st) > 1e-3
+
+
+@pytest.mark.parametrize("d,dims", CASES)
+def test_global_averages_of_an_equilibrium_state(oracle_mod, d, dims):
+    # Eqs. GlobalDensity, GlobalVelocity, GlobalTotalEnergy on an
+    # equilibrium-initialised state.  The discrete equilibrium reproduces
+    # rho, u and eps at every site (its moment constraints, Sec. 3.3), so the
+    # averages are the site means of rho, n u and n (eps + |u|^2 / 2), formed
+    # here from the input fields alone; conservation in time (above) cannot
+    # see a wrong factor in these sums, this pin does.
+    beta0 = 0.9
+    fl = fields.random_fields(d, dims, seed=17)
+    st = oracle_mod.init_equilibrium(d, dims, beta0, fl["rho4"], fl["u"], fl["eps"])
+    c = oracle_mod.conserved(d, dims, beta0, st)
+    n, u, eps = fl["rho4"][0], fl["u"][:d], fl["eps"]
+    assert np.allclose(c[:4], fl["rho4"].mean(axis=1), rtol=0, atol=1e-14)
+    assert np.allclose(c[4:4 + d], (n * u).mean(axis=1), rtol=0, atol=1e-14)
+    assert np.all(c[4 + d:7] == 0.0)
+    assert c[7] == pytest.approx((n * (eps + 0.5 * (u ** 2).sum(axis=0))).mean(), rel=1e-13)
 
 
 @pytest.mark.parametrize("d", [2, 3])
