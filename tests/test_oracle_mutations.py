@@ -67,6 +67,18 @@ MUTATIONS = {
          "double e = L.idx[i][k];\n                mom[k] += e * t;"),
     "velocity not divided by the density (Eq. DiscrAvr)":
         ("M->u[k] = (k < L->d) ? acc / M->n : 0.0;", "M->u[k] = (k < L->d) ? acc : 0.0;"),
+    "eps0 in 3D: the two eta factors swapped (Eq. energyFDstdOmega)":
+        ("1.5 * (1.0 - pow(2.0, -1.5)) * oracle_zeta(2.5) /\n               ((1.0 - pow(2.0, -0.5))",
+         "1.5 * (1.0 - pow(2.0, -0.5)) * oracle_zeta(2.5) /\n               ((1.0 - pow(2.0, -1.5))"),
+    "Pauli read-out: sign of s_y":
+        ("*sy = creal(I * (W->m[0][1] - W->m[1][0]));", "*sy = creal(I * (W->m[1][0] - W->m[0][1]));"),
+    "initial state ignores the given eps field":
+        ("double e = eps ? eps[s] : eps0;", "double e = eps0;"),
+    "adjoint: sign of d omega / d tau":
+        ("double omega = dt / tau, dom_dtau = -dt / (tau * tau);",
+         "double omega = dt / tau, dom_dtau = dt / (tau * tau);"),
+    "FD density prefactor (pi/beta)^(d/2) for (2 pi/beta)^(d/2) (Eq. nFDstdOmega)":
+        ("double h = 0.5 * d, pre = pow(2.0 * M_PI / beta, h);", "double h = 0.5 * d, pre = pow(M_PI / beta, h);"),
     "adjoint read-out: sign of the s_y cotangent":
         ("o[2 * N] = 0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));",
          "o[2 * N] = -0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));"),
