@@ -79,6 +79,13 @@ MUTATIONS = {
          "double omega = dt / tau, dom_dtau = dt / (tau * tau);"),
     "FD density prefactor (pi/beta)^(d/2) for (2 pi/beta)^(d/2) (Eq. nFDstdOmega)":
         ("double h = 0.5 * d, pre = pow(2.0 * M_PI / beta, h);", "double h = 0.5 * d, pre = pow(M_PI / beta, h);"),
+    "alpha2 term without the 1/2 of |e_i|^2/2 (Eq. WeqAlgo)":
+        ("return alpha1 + alpha2 * b0 * 0.5 * e2 +", "return alpha1 + alpha2 * b0 * e2 +"),
+    "equilibrium weighted by the rest weight w_0 in every direction":
+        ("mat_axpy(&Weq[i], L->w[i] * poly_P(L, i, M->u, M->eps), &M->rho);",
+         "mat_axpy(&Weq[i], L->w[0] * poly_P(L, i, M->u, M->eps), &M->rho);"),
+    "diagonal weight of D3Q19 a/4 instead of a/2":
+        ("else L->w[q] = (d == 2) ? L->a / 4.0 : L->a / 2.0;", "else L->w[q] = (d == 2) ? L->a / 4.0 : L->a / 4.0;"),
     "adjoint read-out: sign of the s_y cotangent":
         ("o[2 * N] = 0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));",
          "o[2 * N] = -0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));"),
