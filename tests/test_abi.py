@@ -97,3 +97,19 @@ def test_create_rejects_the_precision_after_the_last(lib):
     with pytest.raises(qlbm.QLBMError) as e:
         qlbm.qlbm_create(2, (4, 4, 1), 0.8, 1.0, 1.0, bad)
     assert e.value.code == qlbm.QLBM_ERR_INVALID_ARG
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    # no CPU fallback: with the library absent, importing the binding raises
+    import subprocess
+    import sys
+    code = ("import paper_1309_1656_gb300._build as b; b.LIB = %r\n"
+            "try:\n"
+            "    import paper_1309_1656_gb300.qlbm\n"
+            "except ImportError as e:\n"
+            "    print('ImportError:', e)\n"
+            "else:\n"
+            "    print('imported')\n") % str(tmp_path / "missing" / "libqlbm.so")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "ImportError: libqlbm.so is not built" in r.stdout, r.stdout
