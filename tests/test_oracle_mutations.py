@@ -86,6 +86,10 @@ MUTATIONS = {
          "mat_axpy(&Weq[i], L->w[0] * poly_P(L, i, M->u, M->eps), &M->rho);"),
     "diagonal weight of D3Q19 a/4 instead of a/2":
         ("else L->w[q] = (d == 2) ? L->a / 4.0 : L->a / 2.0;", "else L->w[q] = (d == 2) ? L->a / 4.0 : L->a / 4.0;"),
+    "FD inversion: density scaled by (beta/pi)^(d/2) for (beta/2 pi)^(d/2)":
+        ("double h = 0.5 * d, y = ns * pow(beta / (2.0 * M_PI), h);", "double h = 0.5 * d, y = ns * pow(beta / M_PI, h);"),
+    "FD inversion: eigenvalue discriminant tr^2/2 for tr^2/4":
+        ("double disc = sqrt(fmax(0.25 * tr * tr - det, 0.0));", "double disc = sqrt(fmax(0.5 * tr * tr - det, 0.0));"),
     "adjoint read-out: sign of the s_y cotangent":
         ("o[2 * N] = 0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));",
          "o[2 * N] = -0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));"),
