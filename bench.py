@@ -12,15 +12,26 @@ ends with the FP64 conservation reduction.  Reported:
   roofline    the step kernel's algorithmic bytes (b*4 values read + written
               per site) / its CUDA-event duration, against the measured HBM
               copy bandwidth
-  fp64        the same for FP64 storage
-  df64        the same for double-float storage (two floats per value,
-              double-float arithmetic on the FP32 pipes)
-  fp64df      the same for FP64 storage stepped in double-float arithmetic
+  fp16dev, fp64, fp64df, df64
+              the same workload in the other storage precisions (FP16
+              deviations; FP64; FP64 stepped in double-float arithmetic;
+              double-float storage), each with its own roofline and clocks
+  d2q9_4096   the D2Q9 4096^2 double shear layer, FP32 and FP16-deviation
+  d3q19_512   the D3Q19 512^3 workload (41 GB FP32 state, tau = 0.6), fields
+              synthesised on the device; MLUPS, GB/s and conservation drift
   e2e         MLUPS through the C ABI with host buffers: init from pinned
               host fields, K steps, moments back to pinned host memory
   adjoint     reverse sweep time (segment recomputation + adjoint steps) /
-              plain forward time over the same 256 steps, FP32
+              plain forward time over the same steps, FP32: the D3Q19
+              192^3 x 2000-step workload with square-root checkpoints (the
+              quoted ratio), and the default workload over 256 steps with
+              every state kept and with square-root checkpoints
+  fd_params   the Fermi-Dirac parameter recovery (FP64 sweep, FD-path step,
+              FP32 step with the fused single-precision solve)
   cpu_baseline  the FP64 oracle on a 32^3 sample on the host cores
+
+Every leg after the first times at least --leg-ms of steps so that the
+nvidia-smi clock samples fall inside its timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent replica (the path has
@@ -126,6 +137,16 @@ class ClockSampler:
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        # wait (at most 3 s) until the sampler is running, so that it covers
+        # the timed region that follows
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 3.0:
+            if self.proc.poll() is not None:
+                break
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -163,22 +184,31 @@ def dist_env():
     return ws, rank, local
 
 
-def run_device(lat, K, W, stream, torch):
-    """W warm-up steps, then K timed steps + the conservation reduction.
-    Returns (step_ms_avg, total_ms)."""
+def time_steps(lat, K, W, stream, torch, min_ms=0.0, ws=1):
+    """W warm-up steps, then the timed region: Kt steps + the conservation
+    reduction, CUDA events on the handle's stream.  Kt = K, or more when
+    min_ms asks for a region long enough for the clock sampler (the per-step
+    time is estimated from 4 extra warm-up steps).  Returns a dict."""
     lat.step(W)
     lat.sync()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e2 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    lat.step(K)
-    e1.record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    Kt = K
+    if min_ms > 0:
+        ev[0].record(stream)
+        lat.step(4)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        est = max(ev[0].elapsed_time(ev[1]) / 4, 1e-4)
+        Kt = max(K, 2 * int(np.ceil(min_ms / est / 2)))
+        Kt = int(max_over_ranks_of(Kt, ws, "cuda"))
+    ev[0].record(stream)
+    lat.step(Kt)
+    ev[1].record(stream)
     cons = lat.conserved()
-    e2.record(stream)
+    ev[2].record(stream)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / K, e0.elapsed_time(e2), cons
+    return dict(steps=Kt, step_ms=ev[0].elapsed_time(ev[1]) / Kt, total_ms=ev[0].elapsed_time(ev[2]), cons=cons)
 
 
 def max_over_ranks_of(x, ws, device):
@@ -194,6 +224,132 @@ def max_over_ranks_of(x, ws, device):
 def job_mlups(ws, sites_per_rank, steps, seconds):
     """Whole-job throughput: all ranks' site updates over the slowest time."""
     return ws * sites_per_rank * steps / seconds / 1e6
+
+
+# Step kernel per precision, and what bounds it when it is not HBM bandwidth.
+STEP_KERNEL = {"fp32": "k_step_aa<%d, CodecF32>", "fp16dev": "k_step_aa_rows<%d, CodecF16Dev>",
+               "fp64": "k_step_aa<%d, CodecF64>", "fp64df": "k_step_aa_f64df<%d>", "df64": "k_step_aa_df2<%d>"}
+STEP_LIMIT = {"fp64": "alu: the FP64 pipe (GB300 issues double arithmetic at 1/64 of the float rate)",
+              "fp64df": "alu: FP64 pipe (pass-1 moment sums, rounding back to double) and integer pipe "
+                        "(double -> double-float splits)"}
+
+
+class Bench:
+    """Shared state of one bench run: device, stream, peaks, ranks."""
+
+    def __init__(self, torch, qlbm, ws, rank, K, W):
+        self.torch, self.qlbm, self.ws, self.rank, self.K, self.W = torch, qlbm, ws, rank, K, W
+        self.peak, self.peak_src = measured_peaks()
+        dev = torch.cuda.current_device()
+        self.stream = torch.cuda.Stream()
+        props = torch.cuda.get_device_properties(dev)
+        uuid = str(getattr(props, "uuid", "")) or str(dev)
+        self.dev_id = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if len(uuid) > 30 else str(dev))
+
+    def barrier(self):
+        if self.ws > 1:
+            self.torch.distributed.barrier()
+
+    def max_over_ranks(self, x):
+        return max_over_ranks_of(x, self.ws, "cuda")
+
+    def lattice(self, d, dims, tau, beta0, prec):
+        return self.qlbm.Lattice(d, dims, tau, beta0, precision=prec, stream=self.stream.cuda_stream)
+
+    def leg(self, d, dims, tau, beta0, prec, init, min_ms=0.0, clocks=True, traffic_key=None):
+        """One storage precision on one workload: init(lat) sets the state;
+        then warm-up, the timed region (clocks sampled during it) and the
+        conservation drift over it.  Returns the leg's record."""
+        torch = self.torch
+        N = dims[0] * dims[1] * dims[2]
+        b = 9 if d == 2 else 19
+        lat = self.lattice(d, dims, tau, beta0, prec)
+        init(lat)
+        c0 = lat.conserved()
+        self.barrier()
+        sampler = ClockSampler(self.dev_id) if clocks else None
+        r = time_steps(lat, self.K, self.W, self.stream, torch, min_ms, self.ws)
+        clk = sampler.stop() if sampler is not None else None
+        lat.close()
+        del lat
+        torch.cuda.synchronize()
+        step_ms = self.max_over_ranks(r["step_ms"])
+        total_ms = self.max_over_ranks(r["total_ms"])
+        alg = N * b * 4 * 2 * bytes_per_value(prec)
+        achieved = alg / (step_ms * 1e-3) / 1e9
+        c1 = r["cons"]
+        drift = float(np.max(np.abs(c1 - c0)) / np.max(np.abs(c0)))
+        tb = recorded_traffic(traffic_key) if traffic_key else None
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": self.peak, "unit": "GB/s",
+                "frac": round(achieved / self.peak, 4), "peak_source": self.peak_src,
+                "traffic": None if tb is None else round(tb * N),
+                "algorithmic_bytes_per_launch": alg, "kernel": STEP_KERNEL[prec] % d}
+        if tb is not None:
+            dram = tb * N / (step_ms * 1e-3) / 1e9
+            roof["dram_achieved"] = round(dram, 1)
+            roof["dram_frac"] = round(dram / self.peak, 4)
+        if prec in STEP_LIMIT:
+            roof["limit"] = STEP_LIMIT[prec]
+        out = {"value": round(job_mlups(self.ws, N, r["steps"], total_ms * 1e-3), 1), "unit": "MLUPS",
+               "steps": r["steps"], "ms_per_step": round(total_ms / r["steps"], 5),
+               "kernel_mlups": round(job_mlups(self.ws, N, 1, step_ms * 1e-3), 1),
+               "roofline": roof, "conservation_drift_rel": drift}
+        if clk:
+            out["clocks"] = clk
+        out["_step_ms"], out["_total_ms"] = step_ms, total_ms
+        return out
+
+    def adjoint(self, d, dims, tau, beta0, fl, NA, interval, box):
+        """Plain forward, recording rollout and reverse sweep over NA FP32
+        steps with checkpoint interval `interval` (0: the library's choice);
+        observable: total s_z over the box (slices per axis)."""
+        torch, qlbm, stream = self.torch, self.qlbm, self.stream
+        N = dims[0] * dims[1] * dims[2]
+        b = 9 if d == 2 else 19
+        lat = self.lattice(d, dims, tau, beta0, "fp32")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        # the plain forward, timed twice (the faster counts: the first run
+        # after large allocations and frees can be slowed by the device)
+        t_plain = float("inf")
+        for _ in range(2):
+            lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+            lat.step(self.W)
+            lat.sync()
+            ev[0].record(stream)
+            lat.step(NA)
+            ev[1].record(stream)
+            lat.sync()
+            t_plain = min(t_plain, ev[0].elapsed_time(ev[1]))
+        # an untimed rollout first allocates the checkpoint memory
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        qlbm.qlbm_rollout(lat.h, NA, interval)
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        qlbm.qlbm_rollout(lat.h, NA, interval)
+        ev[3].record(stream)
+        used = qlbm.qlbm_rollout_interval(lat.h)
+        lam_T = torch.zeros((b, 4, N), dtype=torch.float64, device="cuda")
+        grid = np.zeros(dims[::-1], bool)
+        grid[box[::-1]] = True
+        lam_T[:, 3, torch.from_numpy(grid.ravel()).cuda()] = 1.0
+        lam_0 = torch.empty_like(lam_T)
+        torch.cuda.synchronize()
+        ev[4].record(stream)
+        dJdtau = qlbm.qlbm_rollout_adjoint(lat.h, lam_T, lam_0)
+        ev[5].record(stream)
+        torch.cuda.synchronize()
+        t_plain = self.max_over_ranks(t_plain)
+        t_roll = self.max_over_ranks(ev[2].elapsed_time(ev[3]))
+        t_adj = self.max_over_ranks(ev[4].elapsed_time(ev[5]))
+        lat.close()
+        del lat, lam_T, lam_0
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        return {"ratio": round(t_adj / t_plain, 3), "interval": used, "steps": NA,
+                "forward_ms": round(t_plain, 3), "rollout_ms": round(t_roll, 3), "adjoint_ms": round(t_adj, 3),
+                "rollout_overhead": round(t_roll / t_plain, 3),
+                "rollout_plus_sweep_over_forward": round((t_roll + t_adj) / t_plain, 3), "dJ_dtau": dJdtau}
 
 
 def bench_ours(args):
@@ -212,7 +368,7 @@ def bench_ours(args):
             __graft_entry__.build()
         if ws > 1:
             torch.distributed.barrier()
-    from paper_1309_1656_gb300 import qlbm
+    from paper_1309_1656_gb300 import fields, qlbm
 
     w = WORKLOADS[args.workload]
     d, dims = w["d"], w["dims"]
@@ -220,123 +376,90 @@ def bench_ours(args):
     b = 9 if d == 2 else 19
     K, W = args.steps, args.warmup
     fl = make_fields(w)
-    peak, peak_src = measured_peaks()
-    dev = torch.cuda.current_device()
-    stream = torch.cuda.Stream()
-    props = torch.cuda.get_device_properties(dev)
-    uuid = str(getattr(props, "uuid", "")) or str(dev)
-    dev_id = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if len(uuid) > 30 else str(dev))
+    bn = Bench(torch, qlbm, ws, rank, K, W)
+    stream = bn.stream
+    peak = bn.peak
 
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
+    def init_from(f):
+        return lambda lat: lat.init_equilibrium(f["rho4"], f["u"], f["eps"])
 
-    def max_over_ranks(x):
-        return max_over_ranks_of(x, ws, "cuda")
-
+    # the workload in every storage precision; the first is the line's value
+    precs = args.precisions.split(",")
+    prim = precs[0]
     results = {}
-    clocks = None
-    for prec in args.precisions.split(","):
-        lat = qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision=prec, stream=stream.cuda_stream)
-        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
-        c0 = lat.conserved()
-        barrier()
-        sampler = ClockSampler(dev_id) if prec == "fp32" else None
-        step_ms, total_ms, c1 = run_device(lat, K, W, stream, torch)
-        if sampler is not None:
-            clocks = sampler.stop()
-        step_ms = max_over_ranks(step_ms)
-        total_ms = max_over_ranks(total_ms)
-        alg_bytes = N * b * 4 * 2 * bytes_per_value(prec)
-        achieved = alg_bytes / (step_ms * 1e-3) / 1e9
-        drift = float(np.max(np.abs(c1 - c0)) / np.max(np.abs(c0)))
-        results[prec] = dict(step_ms=step_ms, total_ms=total_ms, achieved=achieved,
-                             mlups=job_mlups(ws, N, K, total_ms * 1e-3),
-                             kernel_mlups=job_mlups(ws, N, 1, step_ms * 1e-3), drift=drift,
-                             alg_bytes=alg_bytes)
-        lat.close()
-        del lat
-        torch.cuda.synchronize()
+    for i, prec in enumerate(precs):
+        results[prec] = bn.leg(d, dims, w["tau"], w["beta0"], prec, init_from(fl),
+                               min_ms=0.0 if i == 0 else args.leg_ms,
+                               traffic_key="step_%s_d%d" % (prec, d))
 
-    # reverse mode: checkpointed rollout + adjoint sweep vs a plain forward
+    # the other workloads: D2Q9 4096^2 shear layer (FP32, FP16-deviation)
+    # and D3Q19 512^3 (FP32), fields synthesised on the device
+    extra = {}
+    if not args.no_extra_workloads:
+        w2 = WORKLOADS["d2q9-4096"]
+        f2 = make_fields(w2)
+        sub = {"workload": w2["desc"], "dims": list(w2["dims"]), "tau": w2["tau"]}
+        for prec in ("fp32", "fp16dev"):
+            sub[prec] = bn.leg(2, w2["dims"], w2["tau"], w2["beta0"], prec, init_from(f2), min_ms=args.leg_ms,
+                               traffic_key="step_%s_d2_4096" % prec)
+        extra["d2q9_4096"] = sub
+        del f2
+        w5 = WORKLOADS["d3q19-512"]
+        spec = fields.mode_spec(3, w5["dims"], seed=w5["seed"])
+        f5 = qlbm.fields_on_device(spec, w5["dims"], stream.cuda_stream)
+        torch.cuda.synchronize()
+        sub = {"workload": w5["desc"] + " (fields synthesised on the device by qlbm_fourier_field)",
+               "dims": list(w5["dims"]), "tau": w5["tau"]}
+        sub["fp32"] = bn.leg(3, w5["dims"], w5["tau"], w5["beta0"], "fp32", init_from(f5), min_ms=args.leg_ms,
+                             traffic_key="step_fp32_d3_512")
+        extra["d3q19_512"] = sub
+        del f5
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    # reverse mode: the 192^3 x 2000-step workload with square-root
+    # checkpoints (the one quoted against the <= 3x target), and the default
+    # workload over 256 steps both with every state kept and with sqrt(N)
+    # checkpoints
     adj = None
-    if "fp32" in results and args.adjoint_steps > 0:
+    if args.adjoint_steps > 0:
+        c = lambda n: slice(n // 2 - max(1, n // 8), n // 2 + max(1, n // 8))
+        box = tuple(c(n) for n in dims)
         NA = args.adjoint_steps
-        lat = qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision="fp32", stream=stream.cuda_stream)
-        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
-        lat.step(W)
-        lat.sync()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-        ev[0].record(stream)
-        lat.step(NA)
-        ev[1].record(stream)
-        lat.sync()
-        # an untimed rollout first allocates the checkpoint memory
-        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
-        qlbm.qlbm_rollout(lat.h, NA, 0)
-        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
-        torch.cuda.synchronize()
-        ev[2].record(stream)
-        qlbm.qlbm_rollout(lat.h, NA, 0)
-        ev[3].record(stream)
-        interval = qlbm.qlbm_rollout_interval(lat.h)
-        # observable: total spin magnetisation s_z in the central (L/4)^d box
-        lam_T = torch.zeros((b, 4, N), dtype=torch.float64, device="cuda")
-        grid = np.zeros(dims[::-1], bool)
-        sl = tuple(slice(n // 2 - max(1, n // 8), n // 2 + max(1, n // 8)) for n in dims[::-1])
-        grid[sl] = True
-        lam_T[:, 3, torch.from_numpy(grid.ravel()).cuda()] = 1.0
-        lam_0 = torch.empty_like(lam_T)
-        torch.cuda.synchronize()
-        ev[4].record(stream)
-        dJdtau = qlbm.qlbm_rollout_adjoint(lat.h, lam_T, lam_0)
-        ev[5].record(stream)
-        torch.cuda.synchronize()
-        t_plain = ev[0].elapsed_time(ev[1])
-        t_roll = ev[2].elapsed_time(ev[3])
-        t_adj = ev[4].elapsed_time(ev[5])
-        t_plain = max_over_ranks(t_plain)
-        t_roll = max_over_ranks(t_roll)
-        t_adj = max_over_ranks(t_adj)
-        # the same with square-root checkpointing forced
-        ksq = 1
-        while ksq * ksq < NA:
-            ksq += 1
-        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
-        qlbm.qlbm_rollout(lat.h, NA, ksq)
-        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
-        torch.cuda.synchronize()
-        ev[2].record(stream)
-        qlbm.qlbm_rollout(lat.h, NA, ksq)
-        ev[3].record(stream)
-        torch.cuda.synchronize()
-        ev[4].record(stream)
-        dJdtau_sq = qlbm.qlbm_rollout_adjoint(lat.h, lam_T, lam_0)
-        ev[5].record(stream)
-        torch.cuda.synchronize()
-        t_roll_sq = max_over_ranks(ev[2].elapsed_time(ev[3]))
-        t_adj_sq = max_over_ranks(ev[4].elapsed_time(ev[5]))
-        adj = {"ratio": round(t_adj / t_plain, 3), "unit": "adjoint sweep time / forward time",
-               "forward_ms": round(t_plain, 3), "rollout_ms": round(t_roll, 3),
-               "adjoint_ms": round(t_adj, 3), "rollout_overhead": round(t_roll / t_plain, 3),
-               "steps": NA, "interval": interval, "precision": "fp32",
-               "observable": "sum of s_z over the central box", "dJ_dtau": dJdtau,
-               "note": "checkpoint interval chosen by the library (1 = every state kept, written by "
-                       "the forward steps; the sweep recomputes nothing)",
-               "sqrt_checkpoints": {"interval": ksq, "ratio": round(t_adj_sq / t_plain, 3),
-                                    "rollout_overhead": round(t_roll_sq / t_plain, 3),
-                                    "adjoint_ms": round(t_adj_sq, 3),
-                                    "dJ_dtau_matches": dJdtau_sq == dJdtau,
-                                    "note": "segment recomputation (two-buffer forward) + reverse steps"}}
-        lat.close()
-        del lat, lam_T, lam_0
-        torch.cuda.synchronize()
+        ksq = int(np.ceil(np.sqrt(NA)))
+        keep = bn.adjoint(d, dims, w["tau"], w["beta0"], fl, NA, 1, box)
+        sq = bn.adjoint(d, dims, w["tau"], w["beta0"], fl, NA, ksq, box)
+        adj = {"unit": "reverse sweep time / plain forward time, same steps",
+               "observable": "total s_z over a central box", "precision": "fp32"}
+        if args.adjoint_big_steps > 0:
+            Lb = 192
+            dimb = (Lb, Lb, Lb)
+            fb = qlbm.fields_on_device(fields.mode_spec(3, dimb, seed=2), dimb, stream.cuda_stream)
+            torch.cuda.synchronize()
+            big = bn.adjoint(3, dimb, 0.7, 1.0, fb, args.adjoint_big_steps, 0,
+                             tuple(slice(Lb // 2 - 16, Lb // 2 + 16) for _ in range(3)))
+            del fb
+            torch.cuda.empty_cache()
+            big["workload"] = ("D3Q19 192^3, tau=0.7, FP32, Fourier-mode fields, %d steps, interval chosen by the "
+                               "library (square-root checkpoints: the states do not fit), observable s_z over the "
+                               "central 32^3 box" % args.adjoint_big_steps)
+            adj["ratio"] = big["ratio"]
+            adj["quoted"] = "sqrt(N) checkpoints on D3Q19 192^3 x %d steps" % args.adjoint_big_steps
+            adj["sqrt_checkpoints_192"] = big
+        else:
+            adj["ratio"] = sq["ratio"]
+            adj["quoted"] = "sqrt(N) checkpoints on the default workload"
+        keep["note"] = "every state kept (written by the forward steps themselves); the sweep recomputes nothing"
+        sq["note"] = "segment recomputation (two-buffer forward) + reverse steps"
+        sq["dJ_dtau_matches_all_states_kept"] = sq["dJ_dtau"] == keep["dJ_dtau"]
+        adj["sqrt_checkpoints"] = sq
+        adj["all_states_kept"] = keep
 
     # Fermi-Dirac parameter recovery (side output, FP64 solve) and the FP64
     # step variant whose equilibrium goes through the recovered parameters
     fdp = None
     if args.fd_params and rank == 0:
-        lat = qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision="fp64", stream=stream.cuda_stream)
+        lat = bn.lattice(d, dims, w["tau"], w["beta0"], "fp64")
         lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
         lat.step(4)
         outs = [torch.empty((N,), dtype=torch.float64, device="cuda") for _ in range(3)]
@@ -368,7 +491,7 @@ def bench_ours(args):
         # the FP32 step with the single-precision solve fused in: every step
         # also writes (beta, mu_up, mu_dn, axis) as float [6][N]
         if "fp32" in results:
-            lat = qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision="fp32", stream=stream.cuda_stream)
+            lat = bn.lattice(d, dims, w["tau"], w["beta0"], "fp32")
             lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
             o32 = [torch.empty((N,), dtype=torch.float32, device="cuda") for _ in range(3)]
             a32 = torch.empty((3, N), dtype=torch.float32, device="cuda")
@@ -387,7 +510,7 @@ def bench_ours(args):
             fbytes = N * (b * 4 * 2 * 4 + 6 * 4)
             fdp["fused_fp32"] = {
                 "step_ms": round(t_f, 4), "mlups": round(N / t_f / 1e3, 1),
-                "vs_plain_step": round(t_f / results["fp32"]["step_ms"], 3),
+                "vs_plain_step": round(t_f / results["fp32"]["_step_ms"], 3),
                 "achieved_gbs": round(fbytes / (t_f * 1e-3) / 1e9, 1),
                 "hbm_frac": round(fbytes / (t_f * 1e-3) / 1e9 / peak, 4),
                 "bytes_per_site": b * 4 * 2 * 4 + 6 * 4, "unresolved_sites": nfail32,
@@ -399,24 +522,24 @@ def bench_ours(args):
 
     # end-to-end through the C ABI with pinned host buffers
     e2e = None
-    if "fp32" in results and not args.no_e2e:
+    if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         r4, uu = pin(fl["rho4"]), pin(fl["u"])
         out_r = torch.empty((4, N), dtype=torch.float64).pin_memory().numpy()
         out_u = torch.empty((d, N), dtype=torch.float64).pin_memory().numpy()
         out_e = torch.empty((N,), dtype=torch.float64).pin_memory().numpy()
-        lat = qlbm.Lattice(d, dims, w["tau"], w["beta0"], precision="fp32", stream=stream.cuda_stream)
+        lat = bn.lattice(d, dims, w["tau"], w["beta0"], prim)
         lat.init_equilibrium(r4, uu)       # warm the staging buffers
         lat.step(W)
         qlbm.qlbm_moments(lat.h, out_r, out_u, out_e)
-        barrier()
+        bn.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         qlbm.qlbm_init_equilibrium(lat.h, r4, uu, None)
         qlbm.qlbm_step(lat.h, K)
         qlbm.qlbm_moments(lat.h, out_r, out_u, out_e)
         t1 = time.perf_counter()
-        dt_e2e = max_over_ranks(t1 - t0)
+        dt_e2e = bn.max_over_ranks(t1 - t0)
         lat.close()
         e2e = {"value": round(job_mlups(ws, N, K, dt_e2e), 3), "unit": "MLUPS",
                "h2d_bytes_per_step": (r4.nbytes + uu.nbytes) / K,
@@ -453,23 +576,13 @@ def bench_ours(args):
     if ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, target_s=args.cpu_seconds, parity_fn=parity)
 
-    r32 = results.get("fp32") or next(iter(results.values()))
-    prim = "fp32" if "fp32" in results else next(iter(results))
-    traffic = recorded_traffic("step_%s_d%d" % (prim, d))
-    roof = {"bound": "hbm", "achieved": round(r32["achieved"], 1), "peak": peak, "unit": "GB/s",
-            "frac": round(r32["achieved"] / peak, 4), "peak_source": peak_src,
-            "traffic": None if traffic is None else round(traffic * N),
-            "algorithmic_bytes_per_launch": r32["alg_bytes"],
-            "kernel": "k_step_aa<%d,%s>" % (d, prim)}
-    if traffic is not None:
-        # DRAM bytes actually moved per launch (ncu) over the same event time:
-        # below the algorithmic bytes by the writes still in L2 at kernel end
-        dram = traffic * N / (r32["step_ms"] * 1e-3) / 1e9
-        roof["dram_achieved"] = round(dram, 1)
-        roof["dram_frac"] = round(dram / peak, 4)
+    def public(r):
+        return {k: v for k, v in r.items() if not k.startswith("_")}
+
+    r0 = results[prim]
     line = {
-        "metric": METRIC, "value": round(r32["mlups"], 1), "unit": "MLUPS", "n_gpus": ws,
-        "steps": K, "warmup": W, "ms_per_step": round(r32["total_ms"] / K, 5),
+        "metric": METRIC, "value": round(job_mlups(ws, N, K, r0["_total_ms"] * 1e-3), 1), "unit": "MLUPS",
+        "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": round(r0["_total_ms"] / K, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16-storage/f32", "df64": "f32x2",
                   "fp64df": "f64-storage/f32x2"}[prim],
@@ -481,28 +594,20 @@ def bench_ours(args):
                           N * b * 4 * bytes_per_value(prim) > 129e6 else
                           "state %.4f GB fits in the 129 MB L2: L2-resident by construction, "
                           "not an HBM measurement") % (N * b * 4 * bytes_per_value(prim) / 1e9)},
-        "roofline": roof,
-        "kernel_mlups": round(r32["kernel_mlups"], 1),
-        "conservation_drift_rel": r32["drift"],
+        "roofline": r0["roofline"],
+        "kernel_mlups": r0["kernel_mlups"],
+        "conservation_drift_rel": r0["conservation_drift_rel"],
         "gpu_launches": K + 2,
     }
+    if "clocks" in r0:
+        line["clocks"] = r0["clocks"]
     for p_, r in results.items():
-        if p_ == prim:
-            continue
-        line[p_] = {"value": round(r["mlups"], 1), "unit": "MLUPS",
-                    "kernel_mlups": round(r["kernel_mlups"], 1),
-                    "achieved_gbs": round(r["achieved"], 1), "hbm_frac": round(r["achieved"] / peak, 4),
-                    "conservation_drift_rel": r["drift"]}
-        if p_ == "fp64":
-            # bound by FP64 issue: 2 FP64 lanes/clk/SM x 152 SMs x clock
-            line[p_]["bound"] = "alu (fp64 pipe, see profiles/k_step_aa_d3q19_fp64_128.md)"
-        if p_ == "fp64df":
-            line[p_]["bound"] = ("alu (fp64 pipe: moment sums and rounding; integer pipe: splits; see "
-                                 "profiles/k_step_aa_f64df_d3q19_fp64df_128.md)")
+        if p_ != prim:
+            line[p_] = public(r)
+    for k_, sub in extra.items():
+        line[k_] = {k: (public(v) if isinstance(v, dict) else v) for k, v in sub.items()}
     if growth:
         line["error_growth"] = growth
-    if clocks:
-        line["clocks"] = clocks
     if e2e:
         line["e2e"] = e2e
     if adj:
@@ -632,7 +737,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="d3q19-128", choices=sorted(WORKLOADS))
-    ap.add_argument("--precisions", default="fp32,fp64,fp64df,df64")
+    ap.add_argument("--precisions", default="fp32,fp16dev,fp64,fp64df,df64",
+                    help="storage precisions of the workload; the first gives the line's value")
+    ap.add_argument("--leg-ms", type=float, default=600.0,
+                    help="least timed-region length of every leg after the first (clock sampling)")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="skip the D2Q9 4096^2 and D3Q19 512^3 legs")
+    ap.add_argument("--adjoint-big-steps", type=int, default=2000,
+                    help="steps of the D3Q19 192^3 reverse-mode leg (0: skip it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -343,6 +343,35 @@ int qlbm_init_equilibrium_adjoint(qlbm_handle h, const double *rho4, const doubl
 int qlbm_conserved_static(int lattice, const int64_t dims[3], double beta0, const double *state,
                           double *out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Synthetic input fields.
+ * ---------------------------------------------------------------------- */
+
+/* qlbm_fourier_field -- a real Fourier sum at every site of a periodic box,
+ * evaluated on the device in double precision:
+ *   out[s] = offset + scale * sum_m (A_m cos(phi_m) + B_m sin(phi_m)),
+ *   phi_m = 2 pi (k_m[0] x / nx + k_m[1] y / ny + k_m[2] z / nz),
+ *   s = x + nx*(y + ny*z).
+ * The paper's method has no counterpart: this generates the smooth, seeded
+ * density / velocity / spin perturbations of the synthetic workloads (the
+ * shape of the smooth initial data of Sec. 4's tests) directly in device
+ * memory, so that a 512^3 field needs neither host memory nor a host FFT.
+ * The coefficients are inputs: nothing random is drawn here.
+ *   dims    {nx, ny, nz}, each in [1, 2^30] (nz = 1 for a 2D box)
+ *   nmodes  number of modes, 0 .. QLBM_FOURIER_MAX_MODES
+ *   k       host, int32 [nmodes][3] integer wave vectors, each component in
+ *           [-QLBM_FOURIER_MAX_K, QLBM_FOURIER_MAX_K]
+ *   A, B    host, double [nmodes] cosine and sine coefficients
+ *   out     device, double [nx*ny*nz], written
+ *   stream  cudaStream_t or NULL; the call is asynchronous on it and
+ *           allocates no memory (the modes travel as a kernel argument)
+ * Deterministic: the result does not depend on the launch.  Errors:
+ * QLBM_ERR_INVALID_ARG, QLBM_ERR_CUDA; message via qlbm_last_error(NULL). */
+#define QLBM_FOURIER_MAX_MODES 512
+#define QLBM_FOURIER_MAX_K 64
+int qlbm_fourier_field(const int64_t dims[3], int nmodes, const int32_t *k, const double *A, const double *B,
+                       double scale, double offset, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

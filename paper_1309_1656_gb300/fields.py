@@ -174,29 +174,39 @@ class ModeField:
         return np.ascontiguousarray(f.real).ravel()
 
 
-def modes(d, dims, seed=2, kmax=4, amp=0.02, umax=0.05, sites=None):
-    """Fourier-mode density / velocity / spin fields (zero-mean perturbations).
-
-    Returns dict(rho4 [4][M], u [d][M], eps=None) on the full grid, or at the
-    given flat ``sites`` only (then M = len(sites))."""
+def mode_spec(d, dims, seed=2, kmax=4, amp=0.02, umax=0.05):
+    """The Fourier-mode workload as data: for each output row a tuple
+    (ModeField, scale, offset), the row's values being offset + scale *
+    field.  dict(rho4=[4 rows], u=[d rows], eps=None)."""
     dims = _dims3(d, dims)
     fn = ModeField(d, dims, seed, 100, kmax)
     fu = [ModeField(d, dims, seed, 200 + c, kmax) for c in range(d)]
     fr = [ModeField(d, dims, seed, 300 + c, kmax) for c in range(3)]
     ub = np.sqrt(sum(f.bound() ** 2 for f in fu))
     uscale = umax / ub
+    rho4 = [(fn, amp / fn.rms(), 1.0)] + [(fr[c], amp / fr[c].rms(), 0.0) for c in range(3)]
+    u = [(fu[c], uscale, 0.0) for c in range(d)]
+    return dict(rho4=rho4, u=u, eps=None)
+
+
+def modes(d, dims, seed=2, kmax=4, amp=0.02, umax=0.05, sites=None):
+    """Fourier-mode density / velocity / spin fields (zero-mean perturbations).
+
+    Returns dict(rho4 [4][M], u [d][M], eps=None) on the full grid, or at the
+    given flat ``sites`` only (then M = len(sites))."""
+    dims = _dims3(d, dims)
+    spec = mode_spec(d, dims, seed, kmax, amp, umax)
 
     def ev(f):
         return f.grid() if sites is None else f.at(sites)
 
     M = int(np.prod(dims)) if sites is None else len(sites)
     rho4 = np.empty((4, M))
-    rho4[0] = 1.0 + (amp / fn.rms()) * ev(fn)
-    for c in range(3):
-        rho4[1 + c] = (amp / fr[c].rms()) * ev(fr[c])
+    for c, (f, scale, offset) in enumerate(spec["rho4"]):
+        rho4[c] = offset + scale * ev(f)
     u = np.empty((d, M))
-    for c in range(d):
-        u[c] = uscale * ev(fu[c])
+    for c, (f, scale, offset) in enumerate(spec["u"]):
+        u[c] = offset + scale * ev(f)
     return dict(rho4=rho4, u=u, eps=None)
 
 

@@ -82,6 +82,12 @@ _init_fd = _sig("qlbm_init_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
 _set_field = _sig("qlbm_set_magnetic_field", _i, [_vp, _d, ctypes.POINTER(_d)])
 _set_eq_path = _sig("qlbm_set_equilibrium_path", _i, [_vp, _i])
 _conserved_static = _sig("qlbm_conserved_static", _i, [_i, ctypes.POINTER(_i64), _d, _vp, _vp, _vp])
+_fourier_field = _sig("qlbm_fourier_field", _i, [ctypes.POINTER(_i64), _i, _vp, _vp, _vp, _d, _d, _vp, _vp])
+
+QLBM_FOURIER_MAX_MODES = 512
+QLBM_FOURIER_MAX_K = 64
+QLBM_STATIC_SCRATCH_BLOCKS = 1024
+QLBM_STATIC_MAX_SITES = 2147483647
 
 
 class QLBMError(RuntimeError):
@@ -97,39 +103,56 @@ def _check(rc, h=None):
     return rc
 
 
-def _ptr(a, kind=None):
-    """(pointer, ptr_kind) of a numpy array or CUDA tensor; None -> NULL."""
+# Geometry of every live handle created through this binding: handle ->
+# (d, b, N, CUDA device ordinal current at creation).  The wrappers check
+# each array's size and device against it before the C call, so that a short
+# array or a tensor on another GPU is refused here instead of being read or
+# written out of bounds by the library.
+_handles = {}
+
+
+def _geom(h):
+    g = _handles.get(h)
+    if g is None:
+        raise ValueError("unknown or destroyed qlbm handle")
+    return g
+
+
+def _ptr(a, n=None, dev=None, dtype=np.float64):
+    """(pointer, ptr_kind) of a numpy array or CUDA tensor; None -> NULL.
+    n: the least number of elements the call reads or writes; dev: the CUDA
+    device ordinal a tensor must live on."""
     if a is None:
-        return None, kind
+        return None, None
     if isinstance(a, np.ndarray):
-        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
-            raise TypeError("host arrays must be C-contiguous float64")
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("host arrays must be C-contiguous %s" % np.dtype(dtype).name)
+        if n is not None and a.size < n:
+            raise ValueError("array of %d elements where %d are needed" % (a.size, n))
         return a.ctypes.data, QLBM_HOST
     # torch tensor
     if not getattr(a, "is_cuda", False):
         raise TypeError("expected a numpy array or a CUDA tensor")
     import torch
-    if a.dtype != torch.float64 or not a.is_contiguous():
-        raise TypeError("device tensors must be contiguous float64")
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    if a.dtype != tdt or not a.is_contiguous():
+        raise TypeError("device tensors must be contiguous %s" % str(tdt))
+    if n is not None and a.numel() < n:
+        raise ValueError("tensor of %d elements where %d are needed" % (a.numel(), n))
+    if dev is not None and a.device.index != dev:
+        raise ValueError("tensor on cuda:%s, the handle lives on cuda:%d" % (a.device.index, dev))
     return a.data_ptr(), QLBM_DEVICE
 
 
-def _ptr32(a):
+def _ptr32(a, n=None, dev=None):
     """(pointer, ptr_kind) of a float32 numpy array or CUDA tensor."""
-    if isinstance(a, np.ndarray):
-        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
-            raise TypeError("host arrays must be C-contiguous float32")
-        return a.ctypes.data, QLBM_HOST
-    if not getattr(a, "is_cuda", False):
-        raise TypeError("expected a numpy array or a CUDA tensor")
-    import torch
-    if a.dtype != torch.float32 or not a.is_contiguous():
-        raise TypeError("device tensors must be contiguous float32")
-    return a.data_ptr(), QLBM_DEVICE
+    return _ptr(a, n, dev, np.float32)
 
 
 def _kind(*ptrs):
     kinds = {k for p, k in ptrs if p is not None}
+    if not kinds:
+        raise TypeError("at least one array argument is required")
     if len(kinds) != 1:
         raise TypeError("all array arguments must live on the same side (host or device)")
     return kinds.pop()
@@ -143,10 +166,14 @@ def qlbm_create(lattice, dims, tau, beta0, dt=1.0, precision=QLBM_FP64, stream=N
     h = _vp()
     _check(_create(ctypes.byref(h), int(lattice), d, float(tau), float(beta0), float(dt),
                    int(precision), _vp(stream) if stream else None))
+    import torch
+    dd = int(lattice)
+    _handles[h.value] = (dd, 9 if dd == 2 else 19, d[0] * d[1] * d[2], torch.cuda.current_device())
     return h.value
 
 
 def qlbm_destroy(h):
+    _handles.pop(h, None)
     _destroy(h)
 
 
@@ -164,7 +191,8 @@ def qlbm_info(h):
 
 
 def qlbm_init_equilibrium(h, rho4, u, eps=None):
-    p = [_ptr(rho4), _ptr(u), _ptr(eps)]
+    d, b, N, dev = _geom(h)
+    p = [_ptr(rho4, 4 * N, dev), _ptr(u, d * N, dev), _ptr(eps, N, dev)]
     _check(_init_eq(h, p[0][0], p[1][0], p[2][0], _kind(*p)), h)
 
 
@@ -181,7 +209,8 @@ def qlbm_sync(h):
 
 
 def qlbm_moments(h, rho4=None, u=None, eps=None):
-    p = [_ptr(rho4), _ptr(u), _ptr(eps)]
+    d, b, N, dev = _geom(h)
+    p = [_ptr(rho4, 4 * N, dev), _ptr(u, d * N, dev), _ptr(eps, N, dev)]
     _check(_moments(h, p[0][0], p[1][0], p[2][0], _kind(*p)), h)
 
 
@@ -192,19 +221,22 @@ def qlbm_conserved(h):
 
 
 def qlbm_get_state(h, buf):
-    p, k = _ptr(buf)
+    d, b, N, dev = _geom(h)
+    p, k = _ptr(buf, b * 4 * N, dev)
     _check(_get_state(h, p, k), h)
     return buf
 
 
 def qlbm_set_state(h, buf):
-    p, k = _ptr(buf)
+    d, b, N, dev = _geom(h)
+    p, k = _ptr(buf, b * 4 * N, dev)
     _check(_set_state(h, p, k), h)
 
 
 def qlbm_step_adjoint(h, lam_next, lam):
     """One reverse step at the current state; fills lam, returns dJ/dtau part."""
-    p = [_ptr(lam_next), _ptr(lam)]
+    d, b, N, dev = _geom(h)
+    p = [_ptr(lam_next, b * 4 * N, dev), _ptr(lam, b * 4 * N, dev)]
     g = _d(0.0)
     _check(_step_adjoint(h, p[0][0], p[1][0], ctypes.byref(g), _kind(*p)), h)
     return g.value
@@ -220,21 +252,25 @@ def qlbm_rollout_interval(h):
 
 def qlbm_rollout_adjoint(h, lam_T, lam_0):
     """Reverse sweep over the last rollout; fills lam_0, returns dJ/dtau."""
-    p = [_ptr(lam_T), _ptr(lam_0)]
+    d, b, N, dev = _geom(h)
+    p = [_ptr(lam_T, b * 4 * N, dev), _ptr(lam_0, b * 4 * N, dev)]
     g = _d(0.0)
     _check(_rollout_adjoint(h, p[0][0], p[1][0], ctypes.byref(g), _kind(*p)), h)
     return g.value
 
 
 def qlbm_init_equilibrium_adjoint(h, rho4, u, eps, lam0, g_rho4=None, g_u=None, g_eps=None):
-    p = [_ptr(rho4), _ptr(u), _ptr(eps), _ptr(lam0), _ptr(g_rho4), _ptr(g_u), _ptr(g_eps)]
+    d, b, N, dev = _geom(h)
+    p = [_ptr(rho4, 4 * N, dev), _ptr(u, d * N, dev), _ptr(eps, N, dev), _ptr(lam0, b * 4 * N, dev),
+         _ptr(g_rho4, 4 * N, dev), _ptr(g_u, d * N, dev), _ptr(g_eps, N, dev)]
     _check(_init_adjoint(h, *[x[0] for x in p], _kind(*p)), h)
 
 
 def qlbm_fd_params(h, beta=None, mu_up=None, mu_dn=None, axis=None):
     """Per-site Fermi-Dirac parameters into the given arrays; returns the
     number of sites without a solution."""
-    p = [_ptr(beta), _ptr(mu_up), _ptr(mu_dn), _ptr(axis)]
+    d, b, N, dev = _geom(h)
+    p = [_ptr(beta, N, dev), _ptr(mu_up, N, dev), _ptr(mu_dn, N, dev), _ptr(axis, 3 * N, dev)]
     nf = _i64(0)
     _check(_fd_params(h, *[x[0] for x in p], ctypes.byref(nf), _kind(*p)), h)
     return nf.value
@@ -244,7 +280,8 @@ def qlbm_step_fd_output(h, beta, mu_up, mu_dn, axis, count=True):
     """One step that also writes the float32 FD parameters of the state it
     started from; returns the number of unresolved sites (None if not
     counted, which keeps device calls asynchronous)."""
-    p = [_ptr32(beta), _ptr32(mu_up), _ptr32(mu_dn), _ptr32(axis)]
+    d, b, N, dev = _geom(h)
+    p = [_ptr32(beta, N, dev), _ptr32(mu_up, N, dev), _ptr32(mu_dn, N, dev), _ptr32(axis, 3 * N, dev)]
     nf = _i64(0)
     _check(_step_fd_output(h, *[x[0] for x in p], ctypes.byref(nf) if count else None, _kind(*p)), h)
     return nf.value if count else None
@@ -252,12 +289,16 @@ def qlbm_step_fd_output(h, beta, mu_up, mu_dn, axis, count=True):
 
 def qlbm_fd_params_adjoint(h, lam, g_beta=None, g_mu_up=None, g_mu_dn=None, g_axis=None):
     """Cotangent of the current state (into lam) from those of the FD parameters."""
-    p = [_ptr(g_beta), _ptr(g_mu_up), _ptr(g_mu_dn), _ptr(g_axis), _ptr(lam)]
+    d, b, N, dev = _geom(h)
+    p = [_ptr(g_beta, N, dev), _ptr(g_mu_up, N, dev), _ptr(g_mu_dn, N, dev), _ptr(g_axis, 3 * N, dev),
+         _ptr(lam, b * 4 * N, dev)]
     _check(_fd_params_adjoint(h, *[x[0] for x in p], _kind(*p)), h)
 
 
 def qlbm_init_fd_params(h, beta, mu_up, mu_dn, axis, u):
-    p = [_ptr(beta), _ptr(mu_up), _ptr(mu_dn), _ptr(axis), _ptr(u)]
+    d, b, N, dev = _geom(h)
+    p = [_ptr(beta, N, dev), _ptr(mu_up, N, dev), _ptr(mu_dn, N, dev), _ptr(axis, 3 * N, dev),
+         _ptr(u, d * N, dev)]
     _check(_init_fd(h, *[x[0] for x in p], _kind(*p)), h)
 
 
@@ -282,11 +323,54 @@ def qlbm_conserved_static(lattice, dims, beta0, state, out, stream=None):
     the GPU race on it.  Asynchronous on ``stream`` (a cudaStream_t value).
     """
     d = (ctypes.c_int64 * 3)(*[int(v) for v in (list(dims) + [1] * (3 - len(dims)))])
-    sp, sk = _ptr(state)
-    op, ok = _ptr(out)
+    import torch
+    dev = torch.cuda.current_device()   # the library reduces on the current device
+    # buffer sizes are checked for dims the library accepts; it rejects the rest itself
+    valid = min(d[0], d[1], d[2]) >= 1 and (int(lattice) != 2 or d[2] == 1) and \
+        d[0] * d[1] * d[2] <= QLBM_STATIC_MAX_SITES
+    nsites = d[0] * d[1] * d[2] if valid else 0
+    sp, sk = _ptr(state, (9 if int(lattice) == 2 else 19) * 4 * nsites, dev)
+    op, ok = _ptr(out, 8, dev)
     if sk != QLBM_DEVICE or ok != QLBM_DEVICE:
         raise TypeError("state and out must be CUDA tensors")
     _check(_conserved_static(int(lattice), d, float(beta0), sp, op, _vp(stream) if stream else None))
+
+
+def qlbm_fourier_field(dims, k, A, B, scale, offset, out, stream=None):
+    """out (CUDA float64 tensor of nx*ny*nz) = offset + scale * sum_m
+    A_m cos(2 pi k_m.x/L) + B_m sin(2 pi k_m.x/L) at every site, evaluated by
+    the library on the device.  k: int [nmodes][3]; A, B: float64 [nmodes]
+    (host arrays).  Asynchronous on ``stream``."""
+    d = (ctypes.c_int64 * 3)(*[int(v) for v in (list(dims) + [1] * (3 - len(dims)))])
+    kk = np.ascontiguousarray(np.asarray(k).reshape(-1, 3), dtype=np.int32)
+    a = np.ascontiguousarray(A, dtype=np.float64).reshape(-1)
+    b = np.ascontiguousarray(B, dtype=np.float64).reshape(-1)
+    if not (len(kk) == len(a) == len(b)):
+        raise ValueError("k, A and B must describe the same number of modes")
+    import torch
+    op, ok = _ptr(out, d[0] * d[1] * d[2], torch.cuda.current_device())
+    if ok != QLBM_DEVICE:
+        raise TypeError("out must be a CUDA tensor")
+    _check(_fourier_field(d, len(kk), kk.ctypes.data, a.ctypes.data, b.ctypes.data, float(scale),
+                          float(offset), op, _vp(stream) if stream else None))
+
+
+def fields_on_device(spec, dims, stream=None):
+    """Device tensors dict(rho4 [4][N], u [d][N], eps=None) of a Fourier-mode
+    workload description (``fields.mode_spec``), each row evaluated by
+    qlbm_fourier_field."""
+    import torch
+    dims = tuple(int(v) for v in (list(dims) + [1] * (3 - len(dims))))
+    N = dims[0] * dims[1] * dims[2]
+    out = {}
+    for key in ("rho4", "u"):
+        rows = spec[key]
+        t = torch.empty((len(rows), N), dtype=torch.float64, device="cuda")
+        for c, (f, scale, offset) in enumerate(rows):
+            qlbm_fourier_field(dims, f.k.astype(np.int32), f.A, f.B, scale, offset, t[c], stream)
+        out[key] = t
+    out["eps"] = None
+    return out
 
 
 class Lattice:
