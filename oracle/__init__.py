@@ -92,6 +92,8 @@ def _load():
         lib.oracle_moments.argtypes = [_i, _pi64, _d, _pd, _pd, _pd, _pd]
         lib.oracle_conserved.restype = _i
         lib.oracle_conserved.argtypes = [_i, _pi64, _d, _pd, _pd]
+        lib.oracle_eq_min_eigenvalues.restype = _i
+        lib.oracle_eq_min_eigenvalues.argtypes = [_i, _pi64, _d, _pd, _pd]
         lib.oracle_adjoint_step.restype = _i
         lib.oracle_adjoint_step.argtypes = [_i, _pi64, _d, _d, _d, _pd, _pd, _pd, _pd, _i]
         lib.oracle_set_field.restype = None
@@ -222,6 +224,27 @@ def conserved(d, dims, beta0, state):
     out = np.zeros(8)
     _check(_load().oracle_conserved(d, cd, beta0, _ptr(st), _ptr(out)), "conserved")
     return out
+
+
+def eq_min_eigenvalues(d, dims, beta0, state):
+    """Smallest eigenvalue of every W_i^eq (Eq. WeqAlgo) built from the
+    state's moments, [b][N] (Sec. 3.2 end: negative values are not clipped)."""
+    cd, N = _dims(d, dims)
+    st = np.ascontiguousarray(state, dtype=np.float64).reshape(nq(d), 4, N)
+    out = np.zeros((nq(d), N))
+    _check(_load().oracle_eq_min_eigenvalues(d, cd, beta0, _ptr(st), _ptr(out)), "eq_min_eigenvalues")
+    return out
+
+
+def negative_eq(d, dims, beta0, state):
+    """(count, mask): the number of (site, direction) pairs whose W_i^eq has a
+    negative eigenvalue, and per site the bit mask of those directions."""
+    lmin = eq_min_eigenvalues(d, dims, beta0, state)
+    neg = lmin < 0.0
+    mask = np.zeros(neg.shape[1], np.uint32)
+    for q in range(neg.shape[0]):
+        mask |= neg[q].astype(np.uint32) << np.uint32(q)
+    return int(neg.sum()), mask
 
 
 def adjoint_step(d, dims, tau, beta0, state, lam_next, dt=1.0, nthreads=0):

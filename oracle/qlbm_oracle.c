@@ -593,6 +593,38 @@ int oracle_conserved(int d, const int64_t *dims, double beta0, const double *sta
     return 0;
 }
 
+/* Smallest eigenvalue of every discrete equilibrium W_i^eq = w_i rho P_i
+   (Eq. WeqAlgo) formed from the moments of the given state, i.e. of the
+   equilibria the next collision relaxes towards.  Sec. 3.2 (end) and
+   Sec. 3.3 (end) note that these can have negative eigenvalues and that the
+   scheme does not clip them; this diagnostic exposes where.  Literally: for
+   the Hermitian 2x2 matrix [[a, c], [conj(c), e]] the eigenvalues are
+   (a + e)/2 -+ sqrt(((a - e)/2)^2 + |c|^2).  out [b][N]. */
+int oracle_eq_min_eigenvalues(int d, const int64_t *dims, double beta0, const double *state, double *out)
+{
+    lattice L;
+    grid G;
+    if (setup_lattice(d, beta0, &L) || setup_grid(d, dims, &G)) return -1;
+    int64_t N = G.N;
+    for (int64_t s = 0; s < N; ++s) {
+        mat2 W[QMAX], Weq[QMAX];
+        for (int i = 0; i < L.b; ++i) {
+            const double *c = state + (int64_t)i * 4 * N + s;
+            pauli_to_mat(c[0], c[N], c[2 * N], c[3 * N], &W[i]);
+        }
+        moments M;
+        site_moments(&L, W, &M);
+        site_equilibrium(&L, &M, Weq);
+        for (int i = 0; i < L.b; ++i) {
+            double a = creal(Weq[i].m[0][0]), e = creal(Weq[i].m[1][1]);
+            double off = cabs(Weq[i].m[0][1]);
+            double half = 0.5 * (a - e);
+            out[(int64_t)i * N + s] = 0.5 * (a + e) - sqrt(half * half + off * off);
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Adjoint (discrete, reverse mode) of one step                               */
 /* ------------------------------------------------------------------------- */

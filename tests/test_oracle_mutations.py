@@ -15,7 +15,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = ["tests/test_oracle_constants.py", "tests/test_oracle_step.py", "tests/test_oracle_fd.py",
-        "tests/test_oracle_field.py"]
+        "tests/test_oracle_field.py", "tests/test_oracle_negative_eq.py"]
 
 # name -> (exact original text, replacement); the original must occur once
 MUTATIONS = {
@@ -90,6 +90,11 @@ MUTATIONS = {
         ("double h = 0.5 * d, y = ns * pow(beta / (2.0 * M_PI), h);", "double h = 0.5 * d, y = ns * pow(beta / M_PI, h);"),
     "FD inversion: eigenvalue discriminant tr^2/2 for tr^2/4":
         ("double disc = sqrt(fmax(0.25 * tr * tr - det, 0.0));", "double disc = sqrt(fmax(0.5 * tr * tr - det, 0.0));"),
+    "equilibrium eigenvalue: the larger one instead of the smaller":
+        ("out[(int64_t)i * N + s] = 0.5 * (a + e) - sqrt(half * half + off * off);",
+         "out[(int64_t)i * N + s] = 0.5 * (a + e) + sqrt(half * half + off * off);"),
+    "equilibrium eigenvalue: off-diagonal entry dropped":
+        ("double off = cabs(Weq[i].m[0][1]);", "double off = 0.0;"),
     "adjoint read-out: sign of the s_y cotangent":
         ("o[2 * N] = 0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));",
          "o[2 * N] = -0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));"),
