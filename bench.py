@@ -266,10 +266,12 @@ class Bench:
         lat = self.lattice(d, dims, tau, beta0, prec)
         init(lat)
         c0 = lat.conserved()
+        neg0 = self.qlbm.qlbm_negative_eq_count(lat.h)
         self.barrier()
         sampler = ClockSampler(self.dev_id) if clocks else None
         r = time_steps(lat, self.K, self.W, self.stream, torch, min_ms, self.ws)
         clk = sampler.stop() if sampler is not None else None
+        neg1 = self.qlbm.qlbm_negative_eq_count(lat.h)
         lat.close()
         del lat
         torch.cuda.synchronize()
@@ -293,7 +295,10 @@ class Bench:
         out = {"value": round(job_mlups(self.ws, N, r["steps"], total_ms * 1e-3), 1), "unit": "MLUPS",
                "steps": r["steps"], "ms_per_step": round(total_ms / r["steps"], 5),
                "kernel_mlups": round(job_mlups(self.ws, N, 1, step_ms * 1e-3), 1),
-               "roofline": roof, "conservation_drift_rel": drift}
+               "roofline": roof, "conservation_drift_rel": drift,
+               "negative_eq_pairs": {"initial": neg0, "final": neg1, "of": N * b,
+                                     "note": "(site, direction) pairs whose W_i^eq has a negative eigenvalue, "
+                                             "before and after the timed steps (never clipped)"}}
         if clk:
             out["clocks"] = clk
         out["_step_ms"], out["_total_ms"] = step_ms, total_ms

@@ -170,6 +170,37 @@ int qlbm_conserved(qlbm_handle h, double *out);
 int qlbm_get_state(qlbm_handle h, double *buf, int ptr_kind);
 int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
 
+/* Round trip through the canonical layout: get_state returns each value of
+ * the storage precision in double; set_state rounds to the storage precision.
+ * The trip get -> set is exact for QLBM_FP64, QLBM_FP64_DF and QLBM_FP16_DEV
+ * (a half deviation survives the double sum with its reference weight and the
+ * subtraction); for QLBM_FP32 it is exact for every spin component and every
+ * trace deviation f_i - w_i of magnitude >= 2^-29, and changes a smaller
+ * nonzero deviation by at most 2^-54 absolute; for QLBM_DF64 a value moves
+ * by at most 2^-48 relative (a double-float pair holds 48 significant bits,
+ * possibly far apart, a double 53 contiguous ones).  For a bit-exact restart
+ * in every precision use the checkpoint image below. */
+
+/* qlbm_checkpoint_bytes -- size in bytes of a checkpoint image of this
+ * handle (-1 for a bad handle). */
+int64_t qlbm_checkpoint_bytes(qlbm_handle h);
+
+/* qlbm_save_checkpoint / qlbm_load_checkpoint -- checkpoint and restart
+ * (Sec. 3.3: the scheme's state at time t is the populations W_i(x,t)).  The
+ * image holds the populations in the storage precision, bit for bit, in
+ * natural order (the AA parity is resolved on saving): b slot planes, each
+ * of N four-component vectors (f, s_x, s_y, s_z) of the storage type, site
+ * fastest (double-float storage: the b planes of hi parts, then the b planes
+ * of lo parts; the deviation codecs store f_i - w_i).  It is valid only for
+ * a handle with the same lattice,
+ * dims and precision.  Stepping a handle loaded from an image taken after k
+ * steps gives, after n more steps, exactly the state of k + n uninterrupted
+ * steps.  buf holds qlbm_checkpoint_bytes(h) bytes on the side ptr_kind
+ * says.  load resets the step counter to 0 (as set_state).  Both calls are
+ * synchronising. */
+int qlbm_save_checkpoint(qlbm_handle h, void *buf, int ptr_kind);
+int qlbm_load_checkpoint(qlbm_handle h, const void *buf, int ptr_kind);
+
 /* qlbm_set_magnetic_field -- adds the Vlasov commutator of an external
  * magnetic field, -i[mu sigma.B, W] (Sec. 5, Eq. sigmaB_comm), as part of
  * the collision: integrated exactly over each time step it is
@@ -179,6 +210,21 @@ int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind);
  * populations in the same fused kernel.  mu = 0 or B = 0 switches it off.
  * Applies to qlbm_step, qlbm_rollout and the reverse mode. */
 int qlbm_set_magnetic_field(qlbm_handle h, double mu, const double B[3]);
+
+/* qlbm_negative_eq_count -- diagnostic of the negative-definite equilibria
+ * that Sec. 3.2 (end) and Sec. 3.3 (end) allow: the discrete equilibrium
+ * W_i^eq = w_i rho P_i (Eq. WeqAlgo) can have a negative eigenvalue, and
+ * the scheme neither clips it nor adapts tau (nor does this library).  From
+ * the current state it forms the moments (Eq. DiscrAvr) and every P_i that
+ * the next collision uses and flags direction i at a site when W_i^eq has a
+ * negative eigenvalue, i.e. when P_i n < |P_i| |S| (the eigenvalues of
+ * w_i P_i rho are w_i P_i (n +- |S|)/2).  The decision is taken in double
+ * whatever the storage precision.  Read only: the state is not changed.
+ *   count  host, receives the number of flagged (site, direction) pairs
+ *   mask   uint32 [N] or NULL: bit i of mask[s] set when direction i is
+ *          flagged at site s (host or device as ptr_kind says)
+ * Every precision.  Synchronising. */
+int qlbm_negative_eq_count(qlbm_handle h, int64_t *count, uint32_t *mask, int ptr_kind);
 
 /* ------------------------------------------------------------------------
  * Fermi-Dirac parameters of the local equilibrium (Sec. 2.2, Prop. 1).
@@ -209,9 +255,14 @@ int qlbm_fd_params(qlbm_handle h, double *beta, double *mu_up, double *mu_dn, do
  * Prop. 1; the collision conserves the moments they depend on), fused into
  * the step kernel: the same solve as qlbm_fd_params in single precision
  * (in double only where the single-precision iteration does not settle).
- * Parameters to ~1e-5 relative; the spin splitting mu_up - mu_dn to ~1e-6
- * |mu| absolute, so near degenerate eigenvalues (|S| << tr rho) use
- * qlbm_fd_params, which solves and returns double.  QLBM_FP32 and
+ * Parameters to 2e-5 relative.  The spin splitting mu_up - mu_dn carries
+ * the float iteration's absolute error whatever |S|: within
+ * 1e-4 |mu_up - mu_dn| + 2e-6 / beta of the double solution for QLBM_FP32
+ * storage (2e-5 / beta for QLBM_FP16_DEV, whose spin components are stored
+ * in half precision), tested for |S| / tr rho down to 1e-8.  Near degenerate
+ * eigenvalues (|S| << tr rho), where that absolute error exceeds the
+ * splitting itself, use qlbm_fd_params, which solves and returns double.
+ * QLBM_FP32 and
  * QLBM_FP16_DEV storage, direct equilibrium path (QLBM_ERR_UNSUPPORTED
  * otherwise).
  *   beta, mu_up, mu_dn  float [N];  axis float [3][N] (zero where |S| = 0);
@@ -290,6 +341,13 @@ int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval);
 /* The checkpoint interval the last qlbm_rollout used (-1: none recorded). */
 int64_t qlbm_rollout_interval(qlbm_handle h);
 
+/* Identifier of the recorded rollout: 1 for the handle's first qlbm_rollout,
+ * incremented by each later one; -1 when none is recorded (none yet, or a
+ * step, init or set_state discarded it).  A caller that keeps several
+ * forward passes apart (e.g. an autograd graph) compares it before calling
+ * qlbm_rollout_adjoint, which always sweeps over the last rollout. */
+int64_t qlbm_rollout_id(qlbm_handle h);
+
 /* qlbm_rollout_adjoint -- reverse sweep over the last qlbm_rollout: for each
  * checkpoint segment, last first, recompute the segment's states from its
  * checkpoint (two-buffer forward steps), then apply the reverse step to them
@@ -335,7 +393,9 @@ int qlbm_init_equilibrium_adjoint(qlbm_handle h, const double *rho4, const doubl
  * (different streams, or different host threads) race on it and must be
  * serialised by the caller.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  No cudaMalloc, cudaFree
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: destroying the device's primary context between
+ * calls (cudaDeviceReset) is not supported.  No cudaMalloc, cudaFree
  * or allocating library routine is called.  Errors: QLBM_ERR_INVALID_ARG,
  * QLBM_ERR_CUDA; message via qlbm_last_error(NULL). */
 #define QLBM_STATIC_SCRATCH_BLOCKS 1024

@@ -1,5 +1,10 @@
 """torch.autograd interface of the checkpointed rollout and its adjoint.
 
+A handle records one rollout at a time: backward() of a graph whose rollout
+is no longer the handle's last one (checked through qlbm_rollout_id) raises
+RuntimeError instead of pairing its saved inputs with another pass's
+checkpoints.
+
 ``rollout(lat, rho4, u, eps, tau, nsteps)`` initialises the handle's state
 from the fields (Eq. WeqAlgo), advances it nsteps with square-root
 checkpointing (``qlbm_rollout``) and returns the final state as a CUDA
@@ -24,6 +29,7 @@ class _Rollout(torch.autograd.Function):
         state = torch.empty((lat.b, 4, lat.N), dtype=torch.float64, device=rho4.device)
         qlbm.qlbm_get_state(lat.h, state)
         ctx.lat = lat
+        ctx.rollout_id = qlbm.qlbm_rollout_id(lat.h)
         ctx.has_eps = eps is not None
         ctx.save_for_backward(rho4, u, eps if eps is not None else rho4.new_empty(0))
         return state
@@ -31,6 +37,12 @@ class _Rollout(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gstate):
         lat = ctx.lat
+        # the handle keeps only its last rollout: refuse to sweep over
+        # another forward pass's checkpoints
+        if qlbm.qlbm_rollout_id(lat.h) != ctx.rollout_id:
+            raise RuntimeError("the handle's recorded rollout is no longer the one this graph's forward pass "
+                               "made (another rollout, step, init or set_state came in between); run the "
+                               "forward pass again before backward")
         rho4, u, eps = ctx.saved_tensors
         eps = eps if ctx.has_eps else None
         lam0 = torch.empty_like(gstate)

@@ -294,6 +294,7 @@ void qlbm_destroy(qlbm_handle h)
     if (h->dtau_acc) cudaFree(h->dtau_acc);
     if (h->scratch_state) cudaFree(h->scratch_state);
     if (h->fd_fail) cudaFree(h->fd_fail);
+    if (h->neg_count) cudaFree(h->neg_count);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     free_rollout(h);
     delete h;
@@ -452,6 +453,50 @@ int qlbm_set_state(qlbm_handle h, const double *buf, int ptr_kind)
     return QLBM_OK;
 }
 
+// A checkpoint image is compact: the natural-order planes without their
+// padding (b planes of N vectors; double-float storage 2b planes).
+namespace {
+int64_t image_planes(const qlbm_ctx *h) { return (int64_t)h->b * (h->prec == QLBM_DF64 ? 2 : 1); }
+size_t vector_bytes(const qlbm_ctx *h) { return 4 * h->elem_bytes / (h->prec == QLBM_DF64 ? 2 : 1); }
+}  // namespace
+
+int64_t qlbm_checkpoint_bytes(qlbm_handle h)
+{
+    return valid(h) ? image_planes(h) * h->g.N * (int64_t)vector_bytes(h) : -1;
+}
+
+int qlbm_save_checkpoint(qlbm_handle h, void *buf, int ptr_kind)
+{
+    if (!valid(h) || !buf) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_save_checkpoint: bad argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    int rc = ensure_staging(h, h->state_bytes());
+    if (rc) return rc;
+    CK(h, h->ops->copy_natural(h, h->staging));
+    const size_t row = (size_t)h->g.N * vector_bytes(h), pitch = (size_t)h->g.P * vector_bytes(h);
+    const cudaMemcpyKind kind = ptr_kind == QLBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    for (int64_t p = 0; p < image_planes(h); ++p)
+        CK(h, cudaMemcpyAsync(static_cast<char *>(buf) + p * row, reinterpret_cast<char *>(h->staging) + p * pitch,
+                              row, kind, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return check_flags(h);
+}
+
+int qlbm_load_checkpoint(qlbm_handle h, const void *buf, int ptr_kind)
+{
+    if (!valid(h) || !buf) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_load_checkpoint: bad argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    const size_t row = (size_t)h->g.N * vector_bytes(h), pitch = (size_t)h->g.P * vector_bytes(h);
+    const cudaMemcpyKind kind = ptr_kind == QLBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    for (int64_t p = 0; p < image_planes(h); ++p)
+        CK(h, cudaMemcpyAsync(static_cast<char *>(h->pop) + p * pitch, static_cast<const char *>(buf) + p * row, row,
+                              kind, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->parity = 0;
+    h->t = 0;
+    h->ro_steps = -1;
+    return QLBM_OK;
+}
+
 int qlbm_step_adjoint(qlbm_handle h, const double *lam_next, double *lam, double *dJ_dtau, int ptr_kind)
 {
     if (!valid(h) || !lam_next || !lam) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_step_adjoint: bad argument");
@@ -548,10 +593,13 @@ int qlbm_rollout(qlbm_handle h, int64_t nsteps, int64_t interval)
     }
     h->ro_steps = nsteps;
     h->ro_interval = K;
+    h->ro_id += 1;
     return QLBM_OK;
 }
 
 int64_t qlbm_rollout_interval(qlbm_handle h) { return (h && h->ro_steps >= 0) ? h->ro_interval : -1; }
+
+int64_t qlbm_rollout_id(qlbm_handle h) { return (h && h->ro_steps >= 0) ? h->ro_id : -1; }
 
 int qlbm_rollout_adjoint(qlbm_handle h, const double *lam_T, double *lam_0, double *dJ_dtau, int ptr_kind)
 {
@@ -750,6 +798,29 @@ int qlbm_step_fd_output(qlbm_handle h, float *beta, float *mu_up, float *mu_dn, 
         return check_flags(h);
     }
     return QLBM_OK;
+}
+
+int qlbm_negative_eq_count(qlbm_handle h, int64_t *count, uint32_t *mask, int ptr_kind)
+{
+    if (!valid(h) || !count) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_negative_eq_count: bad argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    if (!h->neg_count) CK(h, cudaMalloc(&h->neg_count, sizeof(unsigned long long)));
+    CK(h, cudaMemsetAsync(h->neg_count, 0, sizeof(unsigned long long), h->stream));
+    const size_t N = (size_t)h->g.N;
+    unsigned *m = reinterpret_cast<unsigned *>(mask);
+    if (mask && ptr_kind == QLBM_HOST) {
+        int rc = ensure_staging(h, N * sizeof(unsigned));
+        if (rc) return rc;
+        m = reinterpret_cast<unsigned *>(h->staging);
+    }
+    CK(h, h->ops->negative_eq(h, h->neg_count, m));
+    if (mask && ptr_kind == QLBM_HOST)
+        CK(h, cudaMemcpyAsync(mask, m, N * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    unsigned long long c = 0;
+    CK(h, cudaMemcpyAsync(&c, h->neg_count, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *count = (int64_t)c;
+    return check_flags(h);
 }
 
 int qlbm_fd_params_adjoint(qlbm_handle h, const double *g_beta, const double *g_mu_up, const double *g_mu_dn,

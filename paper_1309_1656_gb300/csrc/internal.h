@@ -58,6 +58,7 @@ struct qlbm_ctx {
     void *seg = nullptr;                // rollout segment states (interval - 1 of them)
     int64_t ck_slots = 0, seg_slots = 0;
     int64_t ro_steps = -1, ro_interval = 0;   // last rollout (-1: none)
+    int64_t ro_id = 0;                        // rollouts recorded so far (id of the last one)
     // CUDA graph of kGraphSteps consecutive steps starting from natural order
     cudaGraphExec_t graph = nullptr;
     int use_graph = 1;
@@ -65,6 +66,7 @@ struct qlbm_ctx {
     int mag = 0;                        // magnetic-field term enabled
     double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};   // its per-step spin rotation
     unsigned long long *fd_fail = nullptr;   // device counter of unresolved sites
+    unsigned long long *neg_count = nullptr; // device counter of the negative-equilibrium diagnostic
     size_t state_bytes() const { return (size_t)b * 4 * (size_t)g.P * elem_bytes; }
     size_t lam_bytes() const { return (size_t)b * 4 * (size_t)g.P * (prec == QLBM_FP64 ? 8 : 4); }
 };
@@ -95,6 +97,8 @@ struct LatticeOps {
                            const double *axis, const double *u);
     // single-precision step that also writes the FD parameters (FP32 / FP16 storage; NULL otherwise)
     cudaError_t (*step_fdout)(qlbm_ctx *h, bool odd, float *beta, float *mu_up, float *mu_dn, float *axis);
+    // negative-eigenvalue diagnostic of the equilibria of the current state (every precision)
+    cudaError_t (*negative_eq)(qlbm_ctx *h, unsigned long long *count, unsigned *mask);
 };
 
 // Dispatch tables, one translation unit each (kernels_<lattice>_<codec>.cu).

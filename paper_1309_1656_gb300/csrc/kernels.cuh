@@ -137,6 +137,54 @@ k_moments(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec codec
 }
 
 // ---------------------------------------------------------------------------
+// Negative-definite equilibria (Sec. 3.2 end, Sec. 3.3 end): W_i^eq =
+// w_i rho P_i (Eq. WeqAlgo) can have a negative eigenvalue, and the scheme
+// neither clips it nor adapts tau.  This read-only diagnostic forms, from
+// the current state, the moments and every P_i that the next collision uses
+// and flags direction i when W_i^eq has a negative eigenvalue.  The
+// eigenvalues of w_i P_i rho are w_i P_i (n +- |S|)/2 (w_i > 0), so the
+// smallest is negative exactly when P_i n < |P_i| |S|.  The decision is
+// taken in double whatever the storage precision.  mask[s] (if not NULL)
+// receives bit i for each flagged direction; *count accumulates the number
+// of flagged (site, direction) pairs (one atomic per warp).
+// ---------------------------------------------------------------------------
+template <int D, class Codec, bool SWAPPED>
+__global__ void __launch_bounds__(kStepBlock)
+k_negative_eq(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Codec codec, InitConsts ic,
+              unsigned long long *__restrict__ count, unsigned *__restrict__ mask)
+{
+    using R = typename Codec::R;
+    constexpr int Q = Lattice<D>::Q;
+    SiteIdx si;
+    unsigned m = 0u;
+    if (site_of_block(g, si)) {
+        R f[Q], sx[Q], sy[Q], sz[Q];
+        gather<D, Codec, SWAPPED>(pl, g, si, codec, f, sx, sy, sz);
+        double fd[Q], xd[Q], yd[Q], zd[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int cls = cnorm2<D>(q);
+            fd[q] = codec.to_double(f[q], 0, cls);
+            xd[q] = codec.to_double(sx[q], 1, cls);
+            yd[q] = codec.to_double(sy[q], 2, cls);
+            zd[q] = codec.to_double(sz[q], 3, cls);
+        }
+        const SiteMoments<D, double> mm = site_moments<D, double>(fd, xd, yd, zd);
+        const double jj = mm.jx * mm.jx + mm.jy * mm.jy + mm.jz * mm.jz;
+        const double be = ic.K * (mm.e2n - jj);
+        const double normS = sqrt(mm.Sx * mm.Sx + mm.Sy * mm.Sy + mm.Sz * mm.Sz);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const double P = poly_P_d<D>(ic, q, mm.jx, mm.jy, mm.jz, be);
+            if (P * mm.n < fabs(P) * normS) m |= 1u << q;
+        }
+        if (mask) mask[si.s] = m;
+    }
+    const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)__popc(m));
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
+// ---------------------------------------------------------------------------
 // Global sums of Eqs. GlobalDensity, GlobalVelocity, GlobalTotalEnergy in
 // double: per-block partials, then one block over the partials.  The launch
 // shape is fixed per handle, so the result is deterministic.

@@ -333,6 +333,18 @@ template <int D, class Codec> struct Launchers {
         }
     }
 
+    static cudaError_t negative_eq(qlbm_ctx *h, unsigned long long *count, unsigned *mask)
+    {
+        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+        if (h->parity)
+            k_negative_eq<D, Codec, true><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_codec<Codec>(h),
+                                                                      make_init(h), count, mask);
+        else
+            k_negative_eq<D, Codec, false><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_codec<Codec>(h),
+                                                                       make_init(h), count, mask);
+        return cudaGetLastError();
+    }
+
     // The reverse mode (adjoint, push, cotangent import/export) exists for
     // the FP64, FP32 and FP16 codecs; double-float storage is forward only.
     static const LatticeOps *table()
@@ -341,14 +353,15 @@ template <int D, class Codec> struct Launchers {
             static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
                                          &conserved_partial, nullptr, nullptr, &copy_natural, nullptr,
                                          nullptr, &init_adjoint, &fd_params, nullptr,
-                                         &fd_params_adjoint, &init_fd, nullptr};
+                                         &fd_params_adjoint, &init_fd, nullptr, &negative_eq};
             return &t;
         } else {
             static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
                                          &conserved_partial, &adjoint, &push, &copy_natural, &lam_import,
                                          &lam_export, &init_adjoint, &fd_params,
                                          std::is_same<Codec, CodecF64>::value ? &step_fd : nullptr,
-                                         &fd_params_adjoint, &init_fd, Codec::DEV ? &step_fdout : nullptr};
+                                         &fd_params_adjoint, &init_fd, Codec::DEV ? &step_fdout : nullptr,
+                                         &negative_eq};
             return &t;
         }
     }

@@ -74,6 +74,7 @@ _step_adjoint = _sig("qlbm_step_adjoint", _i, [_vp, _vp, _vp, ctypes.POINTER(_d)
 _rollout = _sig("qlbm_rollout", _i, [_vp, _i64, _i64])
 _rollout_adjoint = _sig("qlbm_rollout_adjoint", _i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i])
 _rollout_interval = _sig("qlbm_rollout_interval", _i64, [_vp])
+_rollout_id = _sig("qlbm_rollout_id", _i64, [_vp])
 _init_adjoint = _sig("qlbm_init_equilibrium_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i])
 _fd_params = _sig("qlbm_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64), _i])
 _fd_params_adjoint = _sig("qlbm_fd_params_adjoint", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
@@ -82,6 +83,10 @@ _init_fd = _sig("qlbm_init_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
 _set_field = _sig("qlbm_set_magnetic_field", _i, [_vp, _d, ctypes.POINTER(_d)])
 _set_eq_path = _sig("qlbm_set_equilibrium_path", _i, [_vp, _i])
 _conserved_static = _sig("qlbm_conserved_static", _i, [_i, ctypes.POINTER(_i64), _d, _vp, _vp, _vp])
+_negative_eq = _sig("qlbm_negative_eq_count", _i, [_vp, ctypes.POINTER(_i64), _vp, _i])
+_checkpoint_bytes = _sig("qlbm_checkpoint_bytes", _i64, [_vp])
+_save_checkpoint = _sig("qlbm_save_checkpoint", _i, [_vp, _vp, _i])
+_load_checkpoint = _sig("qlbm_load_checkpoint", _i, [_vp, _vp, _i])
 _fourier_field = _sig("qlbm_fourier_field", _i, [ctypes.POINTER(_i64), _i, _vp, _vp, _vp, _d, _d, _vp, _vp])
 
 QLBM_FOURIER_MAX_MODES = 512
@@ -233,6 +238,39 @@ def qlbm_set_state(h, buf):
     _check(_set_state(h, p, k), h)
 
 
+def qlbm_checkpoint_bytes(h):
+    _geom(h)
+    return _checkpoint_bytes(h)
+
+
+def _raw(buf, nbytes, dev):
+    """(pointer, ptr_kind) of a byte buffer: a numpy array or CUDA tensor of
+    any dtype holding at least nbytes."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"] or buf.nbytes < nbytes:
+            raise ValueError("checkpoint buffer must be C-contiguous with %d bytes" % nbytes)
+        return buf.ctypes.data, QLBM_HOST
+    if not getattr(buf, "is_cuda", False) or not buf.is_contiguous():
+        raise TypeError("expected a numpy array or a contiguous CUDA tensor")
+    if buf.numel() * buf.element_size() < nbytes or buf.device.index != dev:
+        raise ValueError("checkpoint tensor too small or on another device")
+    return buf.data_ptr(), QLBM_DEVICE
+
+
+def qlbm_save_checkpoint(h, buf):
+    """Bit-exact image of the populations (see qlbm_checkpoint_bytes)."""
+    d, b, N, dev = _geom(h)
+    p, k = _raw(buf, qlbm_checkpoint_bytes(h), dev)
+    _check(_save_checkpoint(h, p, k), h)
+    return buf
+
+
+def qlbm_load_checkpoint(h, buf):
+    d, b, N, dev = _geom(h)
+    p, k = _raw(buf, qlbm_checkpoint_bytes(h), dev)
+    _check(_load_checkpoint(h, p, k), h)
+
+
 def qlbm_step_adjoint(h, lam_next, lam):
     """One reverse step at the current state; fills lam, returns dJ/dtau part."""
     d, b, N, dev = _geom(h)
@@ -248,6 +286,10 @@ def qlbm_rollout(h, nsteps, interval=0):
 
 def qlbm_rollout_interval(h):
     return _rollout_interval(h)
+
+
+def qlbm_rollout_id(h):
+    return _rollout_id(h)
 
 
 def qlbm_rollout_adjoint(h, lam_T, lam_0):
@@ -300,6 +342,30 @@ def qlbm_init_fd_params(h, beta, mu_up, mu_dn, axis, u):
     p = [_ptr(beta, N, dev), _ptr(mu_up, N, dev), _ptr(mu_dn, N, dev), _ptr(axis, 3 * N, dev),
          _ptr(u, d * N, dev)]
     _check(_init_fd(h, *[x[0] for x in p], _kind(*p)), h)
+
+
+def qlbm_negative_eq_count(h, mask=None):
+    """Number of (site, direction) pairs whose discrete equilibrium, formed
+    from the current state, has a negative eigenvalue; mask (optional:
+    uint32 numpy array or int32 CUDA tensor of N) receives the per-site bit
+    masks of those directions."""
+    d, b, N, dev = _geom(h)
+    c = _i64(0)
+    if mask is None:
+        _check(_negative_eq(h, ctypes.byref(c), None, QLBM_HOST), h)
+        return c.value
+    if isinstance(mask, np.ndarray):
+        if mask.dtype != np.uint32 or not mask.flags["C_CONTIGUOUS"] or mask.size < N:
+            raise TypeError("mask must be a C-contiguous uint32 array of N")
+        _check(_negative_eq(h, ctypes.byref(c), mask.ctypes.data, QLBM_HOST), h)
+        return c.value
+    import torch
+    if not getattr(mask, "is_cuda", False) or mask.dtype != torch.int32 or not mask.is_contiguous():
+        raise TypeError("device masks must be contiguous int32 CUDA tensors")
+    if mask.numel() < N or mask.device.index != dev:
+        raise ValueError("mask too short or on another device")
+    _check(_negative_eq(h, ctypes.byref(c), mask.data_ptr(), QLBM_DEVICE), h)
+    return c.value
 
 
 def qlbm_set_magnetic_field(h, mu, B):
@@ -460,6 +526,19 @@ class Lattice:
         axis = np.zeros((3, self.N), np.float32)
         nfail = qlbm_step_fd_output(self.h, beta, mu_up, mu_dn, axis)
         return beta, mu_up, mu_dn, axis, nfail
+
+    def save_checkpoint(self):
+        """Bit-exact checkpoint image (numpy uint8)."""
+        buf = np.zeros(qlbm_checkpoint_bytes(self.h), np.uint8)
+        return qlbm_save_checkpoint(self.h, buf)
+
+    def load_checkpoint(self, buf):
+        qlbm_load_checkpoint(self.h, np.ascontiguousarray(buf))
+
+    def negative_eq(self):
+        """(count, mask uint32 [N]) of the negative-eigenvalue diagnostic."""
+        mask = np.zeros(self.N, np.uint32)
+        return qlbm_negative_eq_count(self.h, mask), mask
 
     def set_magnetic_field(self, mu, B):
         qlbm_set_magnetic_field(self.h, mu, B)

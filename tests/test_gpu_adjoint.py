@@ -264,3 +264,28 @@ def test_autograd_momentum_flux_gradient(q, oracle_mod):
     fdt = (J64(base["rho4"], base["u"], base["eps"], tau + h) -
            J64(base["rho4"], base["u"], base["eps"], tau - h)) / (2 * h)
     assert g_tau == pytest.approx(fdt, rel=2e-4, abs=1e-7)
+
+
+def test_autograd_refuses_a_rollout_it_did_not_record(q):
+    # two forward passes on one handle, then backward of the first: the
+    # handle holds only the second rollout's checkpoints, so backward must
+    # refuse instead of pairing the first graph's inputs with them; the
+    # second graph's backward still works
+    import torch
+    from paper_1309_1656_gb300.autograd import rollout
+    d, dims, T, tau = 2, (20, 16, 1), 6, 0.8
+    fl = fields.random_fields(d, dims, seed=41)
+    r1 = torch.from_numpy(fl["rho4"]).cuda().requires_grad_(True)
+    r2 = torch.from_numpy(fl["rho4"] * 1.01).cuda().requires_grad_(True)
+    u = torch.from_numpy(fl["u"]).cuda()
+    with q.Lattice(d, dims, tau, 1.0, precision="fp64") as lat:
+        s1 = rollout(lat, r1, u, None, tau, T)
+        id1 = q.qlbm_rollout_id(lat.h)
+        s2 = rollout(lat, r2, u, None, tau, T)
+        assert q.qlbm_rollout_id(lat.h) == id1 + 1
+        with pytest.raises(RuntimeError, match="rollout"):
+            s1[:, 3].sum().backward()
+        s2[:, 3].sum().backward()
+        assert r2.grad is not None and torch.isfinite(r2.grad).all()
+        lat.step(1)
+        assert q.qlbm_rollout_id(lat.h) == -1

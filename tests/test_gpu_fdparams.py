@@ -285,3 +285,41 @@ def test_step_fd_output_device_pointers_match_host(q):
             assert np.array_equal(x, y.cpu().numpy())
         assert np.array_equal(host[3], ax.cpu().numpy())
         assert np.array_equal(a.get_state(), b.get_state())
+
+
+@pytest.mark.parametrize("prec,abs_tol,beta_tol", [("fp32", 2e-6, 2e-5), ("fp16dev", 2e-5, 3e-4)])
+@pytest.mark.parametrize("d", [2, 3])
+def test_step_fd_output_splitting_near_degeneracy_vs_oracle(q, oracle_mod, prec, abs_tol, beta_tol, d):
+    # sites with |S|/n log-uniform in [1e-8, 1e-2]: the fused single-
+    # precision output's spin splitting mu_up - mu_dn against the oracle's
+    # double inversion of the same fields (its own init state and moments).
+    # Bound (header of qlbm_step_fd_output): 1e-4 |mu_up - mu_dn| relative
+    # plus abs_tol / beta absolute -- 2e-6 / beta for FP32 storage, 2e-5 /
+    # beta for FP16, whose spin components are stored in half precision
+    # (absolute storage error ~2^-25 per value)
+    dims = (15, 11, 1) if d == 2 else (7, 6, 4)
+    N = int(np.prod(dims))
+    fl = fields.modes(d, dims, seed=19, amp=0.05, umax=0.1)
+    rng = np.random.default_rng(29 + d)
+    ratio = 10.0 ** rng.uniform(-8, -2, N)
+    ax = rng.normal(size=(3, N))
+    ax /= np.linalg.norm(ax, axis=0)
+    fl["rho4"][1:] = ratio * fl["rho4"][0] * ax
+    with q.Lattice(d, dims, 0.7, 1.0, precision=prec) as lat:
+        lat.init_equilibrium(fl["rho4"], fl["u"], fl["eps"])
+        b, mu, md, axg, nf = lat.step_fd_output()
+    assert nf == 0
+    st = oracle_mod.init_equilibrium(d, dims, 1.0, fl["rho4"], fl["u"], fl["eps"])
+    r4, _, eps = oracle_mod.moments(d, dims, 1.0, st)
+    worst = 0.0
+    for s in range(N):
+        rc, out = oracle_mod.fd_params(d, r4[:, s], eps[s])
+        assert rc == 0
+        split_o = out[1] - out[2]
+        split_g = float(mu[s]) - float(md[s])
+        bound = 1e-4 * abs(split_o) + abs_tol / out[0]
+        worst = max(worst, abs(split_g - split_o) / bound)
+        assert abs(split_g - split_o) <= bound, (s, ratio[s], split_g, split_o)
+        # beta against the oracle's: FP16 storage rounds the energy moments
+        assert float(b[s]) == pytest.approx(out[0], rel=beta_tol)
+    assert worst <= 1.0

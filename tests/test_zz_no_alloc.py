@@ -5,7 +5,9 @@ conserved sums (code under another component's memory manager, or loops
 that cannot afford cudaMalloc/cudaFree).  This test calls it through the C
 ABI on caller-owned device buffers and checks it against qlbm_conserved,
 which computes the same averages from the handle's own buffer, on two
-calls in a row sharing the library's fixed scratch array.  The file name
+calls in a row sharing the library's fixed scratch array, and against the
+FP64 oracle on host-generated states, including lattices larger than one
+pass of the fixed scratch and a call on a non-default stream.  The file name
 makes pytest collect it last; it also runs alone in a fresh process.
 """
 import numpy as np
@@ -30,7 +32,7 @@ def q():
 
 
 @pytest.mark.parametrize("d,dims", [(2, (130, 37, 1)), (3, (33, 20, 9))])
-def test_conserved_static_matches_conserved(q, d, dims):
+def test_conserved_static_matches_conserved(q, oracle_mod, d, dims):
     import torch
     b = 9 if d == 2 else 19
     N = int(np.prod(dims))
@@ -51,6 +53,41 @@ def test_conserved_static_matches_conserved(q, d, dims):
             assert np.all(np.isfinite(got)), call
             assert np.max(np.abs(got - ref)) <= 1e-12 * scale, (call, got, ref)
             lat.step(2)  # the second call sees a different state
+    # and against the oracle on a host-generated state
+    st = fields.random_populations(d, dims, seed=33)
+    state = torch.from_numpy(st).cuda()
+    q.qlbm_conserved_static(d, dims, beta0, state, out)
+    torch.cuda.synchronize()
+    ref = oracle_mod.conserved(d, dims, beta0, st)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("d,dims", [(2, (600, 500, 1)), (3, (70, 66, 61))])
+def test_conserved_static_large_lattice_vs_oracle(q, oracle_mod, d, dims):
+    # more sites than the fixed scratch's blocks cover in one pass (1024
+    # blocks of 256 threads), so the grid-stride loop runs more than once;
+    # the state is generated on the host and the same array goes to the
+    # oracle; one call on a non-default stream, one on the default stream
+    import torch
+    N = int(np.prod(dims))
+    assert N > q.QLBM_STATIC_SCRATCH_BLOCKS * 256
+    beta0 = 0.9
+    st = fields.random_populations(d, dims, seed=32 + d)
+    ref = oracle_mod.conserved(d, dims, beta0, st)
+    state = torch.from_numpy(st).cuda()
+    out = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    for stream in (s.cuda_stream, None):
+        out.fill_(float("nan"))
+        torch.cuda.synchronize()
+        q.qlbm_conserved_static(d, dims, beta0, state, out, stream)
+        if stream is not None:
+            s.synchronize()
+        else:
+            torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), (stream, got, ref)
 
 
 def test_conserved_static_rejects_bad_sizes(q):
