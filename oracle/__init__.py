@@ -98,6 +98,8 @@ def _load():
         lib.oracle_adjoint_step.argtypes = [_i, _pi64, _d, _d, _d, _pd, _pd, _pd, _pd, _i]
         lib.oracle_set_field.restype = None
         lib.oracle_set_field.argtypes = [_d, _d, _d, _d]
+        lib.oracle_set_field_array.restype = _i
+        lib.oracle_set_field_array.argtypes = [_d, _pd, _i64]
         lib.oracle_fd.restype = _d
         lib.oracle_fd.argtypes = [_d, _d]
         lib.oracle_fd_moments.restype = _i
@@ -283,3 +285,13 @@ def fd_params(d, rho4, eps):
 def set_field(mu, B):
     """Uniform external magnetic field for the following runs (mu = 0: off)."""
     _load().oracle_set_field(float(mu), float(B[0]), float(B[1]), float(B[2]))
+
+
+def set_field_array(mu, B):
+    """Per-site external magnetic field B [3][N] for the following runs on
+    N-site lattices (None: off)."""
+    if B is None:
+        _check(_load().oracle_set_field_array(0.0, None, 0), "set_field_array")
+        return
+    b = np.ascontiguousarray(B, dtype=np.float64).reshape(3, -1)
+    _check(_load().oracle_set_field_array(float(mu), _ptr(b), b.shape[1]), "set_field_array")

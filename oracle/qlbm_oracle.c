@@ -283,29 +283,60 @@ static void site_collide(const lattice *L, double omega, const mat2 *W, mat2 *Wc
 /* -i[mu sigma.B, W] added to the collision, integrated exactly over one     */
 /* time step: W -> U W U*, U = exp(-i mu dt sigma.B)                          */
 /*   = cos(phi) 1 - i sin(phi) (b.sigma), phi = mu dt |B|, b = B/|B|.          */
-/* Off unless oracle_set_field is called with mu |B| != 0.                    */
+/* The field is one vector for the whole lattice (oracle_set_field) or one   */
+/* per site, B(x) (oracle_set_field_array); U then depends on the site.      */
+/* Off unless one of the two is set with mu |B| != 0.                         */
 /* ------------------------------------------------------------------------- */
 static double field_mu = 0.0, field_B[3] = {0.0, 0.0, 0.0};
+static double *field_B_site = NULL;   /* [3][field_N], or NULL: uniform */
+static int64_t field_N = 0;
 
 void oracle_set_field(double mu, double Bx, double By, double Bz)
 {
+    free(field_B_site);
+    field_B_site = NULL;
+    field_N = 0;
     field_mu = mu;
     field_B[0] = Bx;
     field_B[1] = By;
     field_B[2] = Bz;
 }
 
-static int field_unitary(double dt, mat2 *U)
+/* B [3][N]: B_x, B_y, B_z of every site; NULL switches the field off. */
+int oracle_set_field_array(double mu, const double *B, int64_t N)
 {
-    double nb = sqrt(field_B[0] * field_B[0] + field_B[1] * field_B[1] + field_B[2] * field_B[2]);
+    free(field_B_site);
+    field_B_site = NULL;
+    field_N = 0;
+    field_mu = 0.0;
+    field_B[0] = field_B[1] = field_B[2] = 0.0;
+    if (!B || N <= 0) return 0;
+    field_B_site = (double *)malloc(3 * (size_t)N * sizeof(double));
+    if (!field_B_site) return -2;
+    memcpy(field_B_site, B, 3 * (size_t)N * sizeof(double));
+    field_N = N;
+    field_mu = mu;
+    return 0;
+}
+
+/* The per-site field must cover the lattice it is used on. */
+static int field_fits(int64_t N) { return field_B_site == NULL || field_N == N; }
+
+/* U at site s of an N-site lattice; returns 0 (and leaves U) where the
+   field vanishes. */
+static int field_unitary(double dt, int64_t s, int64_t N, mat2 *U)
+{
+    double B[3];
+    for (int k = 0; k < 3; ++k) B[k] = field_B_site ? field_B_site[(int64_t)k * N + s] : field_B[k];
+    double nb = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
     if (!(nb > 0.0) || field_mu == 0.0) return 0;
-    double phi = field_mu * dt * nb, c = cos(phi), s = sin(phi);
-    double bx = field_B[0] / nb, by = field_B[1] / nb, bz = field_B[2] / nb;
+    double phi = field_mu * dt * nb, c = cos(phi), sn = sin(phi);
+    double bx = B[0] / nb, by = B[1] / nb, bz = B[2] / nb;
     /* b.sigma = [[bz, bx - i by], [bx + i by, -bz]] */
-    U->m[0][0] = c - I * s * bz;
-    U->m[0][1] = -I * s * (bx - I * by);
-    U->m[1][0] = -I * s * (bx + I * by);
-    U->m[1][1] = c + I * s * bz;
+    U->m[0][0] = c - I * sn * bz;
+    U->m[0][1] = -I * sn * (bx - I * by);
+    U->m[1][0] = -I * sn * (bx + I * by);
+    U->m[1][1] = c + I * sn * bz;
     return 1;
 }
 
@@ -399,15 +430,14 @@ static void step_matrix(const lattice *L, const grid *G, double omega, double dt
 {
     int64_t N = G->N;
     int b = L->b;
-    mat2 U, Ud;
-    int field = field_unitary(dt, &U);
-    if (field) mat_adjoint(&U, &Ud);
 #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < N; ++s) {
-        mat2 Wc[QMAX];
+        mat2 Wc[QMAX], U, Ud;
         site_collide(L, omega, &src[s * b], Wc);
-        if (field)
-            for (int i = 0; i < b; ++i) mat_sandwich(&U, &Wc[i], &Ud);   /* W -> U W U* */
+        if (field_unitary(dt, s, N, &U)) {
+            mat_adjoint(&U, &Ud);
+            for (int i = 0; i < b; ++i) mat_sandwich(&U, &Wc[i], &Ud);   /* W -> U(x) W U(x)* */
+        }
         for (int i = 0; i < b; ++i) {
             int64_t t = shift_site(G, s, L->idx[i][0], L->idx[i][1], L->idx[i][2]);
             dst[t * b + i] = Wc[i];
@@ -423,7 +453,7 @@ int oracle_run_matrix(int d, const int64_t *dims, double tau, double beta0, doub
     lattice L;
     grid G;
     if (setup_lattice(d, beta0, &L) || setup_grid(d, dims, &G)) return -1;
-    if (!(tau > 0.0) || !(dt >= 0.0) || nsteps < 0) return -1;
+    if (!(tau > 0.0) || !(dt >= 0.0) || nsteps < 0 || !field_fits(G.N)) return -1;
     set_threads(nthreads);
     double omega = dt / tau;
     size_t bytes = (size_t)G.N * L.b * sizeof(mat2);
@@ -716,12 +746,12 @@ int oracle_adjoint_step(int d, const int64_t *dims, double tau, double beta0, do
     int b = L.b;
     double omega = dt / tau, dom_dtau = -dt / (tau * tau);
     double total = 0.0;
-    mat2 U, Ud;
-    int field = field_unitary(dt, &U);
-    if (field) mat_adjoint(&U, &Ud);
+    if (!field_fits(N)) return -1;
 #pragma omp parallel for schedule(static) reduction(+ : total)
     for (int64_t s = 0; s < N; ++s) {
-        mat2 W[QMAX], Lp[QMAX], Lo[QMAX];
+        mat2 W[QMAX], Lp[QMAX], Lo[QMAX], U, Ud;
+        int field = field_unitary(dt, s, N, &U);
+        if (field) mat_adjoint(&U, &Ud);
         for (int i = 0; i < b; ++i) {
             const double *c = state + (int64_t)i * 4 * N + s;
             pauli_to_mat(c[0], c[N], c[2 * N], c[3 * N], &W[i]);

@@ -59,7 +59,7 @@ MUTATIONS = {
     "FD inversion: Bloch axis y component of the conjugate":
         ("out[4] = 2.0 * cimag(conj(v0) * v1);", "out[4] = -2.0 * cimag(conj(v0) * v1);"),
     "field: rotation of the wrong sense":
-        ("U->m[0][0] = c - I * s * bz;", "U->m[0][0] = c + I * s * bz;"),
+        ("U->m[0][0] = c - I * sn * bz;", "U->m[0][0] = c + I * sn * bz;"),
     "global energy without the 1/2 (Eq. GlobalTotalEnergy)":
         ("en += 0.5 * e2 * t;", "en += e2 * t;"),
     "global momentum without the lattice constant xi (Eq. GlobalVelocity)":
@@ -95,6 +95,12 @@ MUTATIONS = {
          "out[(int64_t)i * N + s] = 0.5 * (a + e) + sqrt(half * half + off * off);"),
     "equilibrium eigenvalue: off-diagonal entry dropped":
         ("double off = cabs(Weq[i].m[0][1]);", "double off = 0.0;"),
+    "per-site field read from the wrong site's column":
+        ("B[k] = field_B_site ? field_B_site[(int64_t)k * N + s] : field_B[k];",
+         "B[k] = field_B_site ? field_B_site[(int64_t)k * N + (s + 1) % N] : field_B[k];"),
+    "per-site field components transposed (x read as y)":
+        ("B[k] = field_B_site ? field_B_site[(int64_t)k * N + s] : field_B[k];",
+         "B[k] = field_B_site ? field_B_site[(int64_t)((k + 1) % 3) * N + s] : field_B[k];"),
     "adjoint read-out: sign of the s_y cotangent":
         ("o[2 * N] = 0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));",
          "o[2 * N] = -0.5 * creal(I * (Lo[i].m[0][1] - Lo[i].m[1][0]));"),
