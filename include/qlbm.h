@@ -205,11 +205,35 @@ int qlbm_load_checkpoint(qlbm_handle h, const void *buf, int ptr_kind);
  * magnetic field, -i[mu sigma.B, W] (Sec. 5, Eq. sigmaB_comm), as part of
  * the collision: integrated exactly over each time step it is
  * W_i -> U W_i U*, U = exp(-i mu dt sigma.B), a rotation of every Bloch
- * vector s_i by 2 mu |B| dt about B.  The field is uniform; it commutes with
- * the SU(2)-covariant collision, so it is applied to the post-collision
- * populations in the same fused kernel.  mu = 0 or B = 0 switches it off.
- * Applies to qlbm_step, qlbm_rollout and the reverse mode. */
+ * vector s_i by 2 mu |B| dt about B.  This call sets one field for the
+ * whole lattice; it commutes with the SU(2)-covariant collision, so it is
+ * applied to the post-collision populations in the same fused kernel.
+ * mu = 0 or B = 0 switches it off (and so replaces a per-site field).
+ * Applies to qlbm_step (both equilibrium paths), qlbm_step_fd_output,
+ * qlbm_rollout and the reverse mode.  Discards a recorded rollout. */
 int qlbm_set_magnetic_field(qlbm_handle h, double mu, const double B[3]);
+
+/* qlbm_set_magnetic_field_array -- the same term with a field that varies
+ * over the lattice, -i[mu sigma.B(x), W] (Sec. 5, Eq. sigmaB_comm): every
+ * post-collision Bloch vector at site x is rotated by 2 mu |B(x)| dt about
+ * B(x), exactly U(x) W U(x)* with U(x) = exp(-i mu dt sigma.B(x)).  Still
+ * a rotation per site, it commutes with that site's collision, so it is
+ * applied in the same fused kernels.
+ *   mu  magnetic moment (finite)
+ *   B   double [3][N]: B_x, B_y, B_z of every site (host or device, as
+ *       ptr_kind says); non-finite values are refused with
+ *       QLBM_ERR_INVALID_ARG and leave the field off
+ * The library keeps, per site, the unit quaternion (cos phi, sin phi
+ * B/|B|), phi = mu |B(x)| dt (16 bytes in single-precision storage, 32 in
+ * FP64), which each step reads once per site.  A field B(x, t) that changes
+ * in time is given by calling this again between steps: the new field
+ * applies from the next step.  Applies to qlbm_step (both equilibrium
+ * paths), qlbm_step_fd_output, qlbm_rollout and the reverse mode (which
+ * uses the field set when the rollout was recorded: a call discards a
+ * recorded rollout).  QLBM_FP64, QLBM_FP32 and QLBM_FP16_DEV storage
+ * (QLBM_ERR_UNSUPPORTED otherwise).  qlbm_set_magnetic_field replaces it.
+ * Synchronising. */
+int qlbm_set_magnetic_field_array(qlbm_handle h, double mu, const double *B, int ptr_kind);
 
 /* qlbm_negative_eq_count -- diagnostic of the negative-definite equilibria
  * that Sec. 3.2 (end) and Sec. 3.3 (end) allow: the discrete equilibrium

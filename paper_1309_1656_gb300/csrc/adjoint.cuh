@@ -143,11 +143,12 @@ __device__ __forceinline__ void unrotate(R &mx, R &my, R &mz, const R (&rot)[9])
     mz = rot[2] * x + rot[5] * y + rot[8] * z;
 }
 
-template <int D, class Codec, int q, bool MAG>
+template <int D, class Codec, int q, int FIELD>
 __device__ __forceinline__ void adj_accumulate(const Planes<typename Codec::S, Lattice<D>::Q> &st,
                                                const Planes<typename Codec::R, Lattice<D>::Q> &lin,
                                                const Grid &g, const SiteIdx &si, const Codec &codec,
-                                               const Coll<typename Codec::R> &k, typename Codec::R (&fw)[8],
+                                               const Coll<typename Codec::R> &k,
+                                               const typename Codec::R (&rot)[9], typename Codec::R (&fw)[8],
                                                typename Codec::R &dot, MuMom<typename Codec::R> &A,
                                                MuMom<typename Codec::R> &Bx, MuMom<typename Codec::R> &By,
                                                MuMom<typename Codec::R> &Bz)
@@ -158,7 +159,7 @@ __device__ __forceinline__ void adj_accumulate(const Planes<typename Codec::S, L
     const int s = neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q));
     R mf, mx, my, mz;
     ldq(lin.p[q] + s, mf, mx, my, mz);
-    if constexpr (MAG) unrotate(mx, my, mz, k.rot);
+    if constexpr (FIELD != FIELD_NONE) unrotate(mx, my, mz, rot);
     fw[0] += f;
     fw[1] += sx;
     fw[2] += sy;
@@ -175,25 +176,27 @@ __device__ __forceinline__ void adj_accumulate(const Planes<typename Codec::S, L
     Bz.template add<D, q>(w * mz);
 }
 
-template <int D, class Codec, int q, bool MAG>
+template <int D, class Codec, int q, int FIELD>
 struct AdjLoop {
     static __device__ __forceinline__ void run(const Planes<typename Codec::S, Lattice<D>::Q> &st,
                                                const Planes<typename Codec::R, Lattice<D>::Q> &lin,
                                                const Grid &g, const SiteIdx &si, const Codec &codec,
-                                               const Coll<typename Codec::R> &k, typename Codec::R (&fw)[8],
+                                               const Coll<typename Codec::R> &k,
+                                               const typename Codec::R (&rot)[9], typename Codec::R (&fw)[8],
                                                typename Codec::R &dot, MuMom<typename Codec::R> &A,
                                                MuMom<typename Codec::R> &Bx, MuMom<typename Codec::R> &By,
                                                MuMom<typename Codec::R> &Bz)
     {
-        adj_accumulate<D, Codec, q, MAG>(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
-        AdjLoop<D, Codec, q + 1, MAG>::run(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
+        adj_accumulate<D, Codec, q, FIELD>(st, lin, g, si, codec, k, rot, fw, dot, A, Bx, By, Bz);
+        AdjLoop<D, Codec, q + 1, FIELD>::run(st, lin, g, si, codec, k, rot, fw, dot, A, Bx, By, Bz);
     }
 };
-template <int D, class Codec, bool MAG> struct AdjLoop<D, Codec, Lattice<D>::Q, MAG> {
+template <int D, class Codec, int FIELD> struct AdjLoop<D, Codec, Lattice<D>::Q, FIELD> {
     static __device__ __forceinline__ void run(const Planes<typename Codec::S, Lattice<D>::Q> &,
                                                const Planes<typename Codec::R, Lattice<D>::Q> &,
                                                const Grid &, const SiteIdx &, const Codec &,
-                                               const Coll<typename Codec::R> &, typename Codec::R (&)[8],
+                                               const Coll<typename Codec::R> &,
+                                               const typename Codec::R (&)[9], typename Codec::R (&)[8],
                                                typename Codec::R &, MuMom<typename Codec::R> &,
                                                MuMom<typename Codec::R> &, MuMom<typename Codec::R> &,
                                                MuMom<typename Codec::R> &)
@@ -213,7 +216,7 @@ template <int D, class Codec, bool MAG> struct AdjLoop<D, Codec, Lattice<D>::Q, 
 // are known.  Pass 2 re-reads mu (cache hits; the index carries the
 // run-time zero so the compiler does not keep pass 1's values live) and
 // writes lambda^n.
-template <int D, class Codec, bool MAG>
+template <int D, class Codec, int FIELD>
 __global__ void __launch_bounds__(kAdjBlock, Codec::MIN_BLOCKS)
 k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typename Codec::R, Lattice<D>::Q> lin,
           const Planes<typename Codec::R, Lattice<D>::Q> lout, Grid g, Coll<typename Codec::R> k,
@@ -233,7 +236,11 @@ k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typena
         Bx.zero();
         By.zero();
         Bz.zero();
-        AdjLoop<D, Codec, 0, MAG>::run(st, lin, g, si, codec, k, fw, dot, A, Bx, By, Bz);
+        // the field term's rotation at this site (the forward step rotates
+        // the spins collided here; their cotangents take its transpose)
+        R rot[9];
+        if constexpr (FIELD != FIELD_NONE) field_rotation<FIELD>(k, si.s, rot);
+        AdjLoop<D, Codec, 0, FIELD>::run(st, lin, g, si, codec, k, rot, fw, dot, A, Bx, By, Bz);
         // forward moments
         const R dn = DEV ? fw[0] : fw[0] - R(1);
         const R n = DEV ? R(1) + fw[0] : fw[0];
@@ -296,7 +303,7 @@ k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typena
             const int s = neighbour(g, s2, cx<D>(q), cy<D>(q), cz<D>(q));
             R mf, mx, my, mz;
             ldq(lin.p[q] + s, mf, mx, my, mz);
-            if constexpr (MAG) unrotate(mx, my, mz, k.rot);
+            if constexpr (FIELD != FIELD_NONE) unrotate(mx, my, mz, rot);
             stq(lout.p[q] + s2.s,
                 omc * mf + nbar + (cx<D>(q) * Jbx2 + cy<D>(q) * Jby2 + cz<D>(q) * Jbz2) + cnorm2<D>(q) * Eb,
                 omc * mx + Sbx, omc * my + Sby, omc * mz + Sbz);
@@ -308,7 +315,7 @@ k_adjoint(const Planes<typename Codec::S, Lattice<D>::Q> st, const Planes<typena
 
 // Two-buffer forward step (push): src and dst in natural order.  Used to
 // recompute the states inside a checkpoint segment.
-template <int D, class Codec, bool MAG>
+template <int D, class Codec, int FIELD>
 __global__ void __launch_bounds__(kStepBlock, Codec::MIN_BLOCKS)
 k_step_push(const Planes<typename Codec::S, Lattice<D>::Q> src, const Planes<typename Codec::S, Lattice<D>::Q> dst,
             Grid g, Coll<typename Codec::R> k, Codec codec, unsigned *__restrict__ flags)
@@ -320,7 +327,7 @@ k_step_push(const Planes<typename Codec::S, Lattice<D>::Q> src, const Planes<typ
     R f[Q], sx[Q], sy[Q], sz[Q];
     gather<D, Codec, false>(src, g, si, codec, f, sx, sy, sz);
     const unsigned flag = Codec::template collide<D>(f, sx, sy, sz, k);
-    if constexpr (MAG) rotate_spins<D, R>(sx, sy, sz, k.rot);
+    apply_field<D, FIELD, R>(sx, sy, sz, k, si.s);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int s = neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q));

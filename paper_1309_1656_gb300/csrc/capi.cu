@@ -200,6 +200,44 @@ k_conserved_final(const double *__restrict__ partials, int nparts, double xi, in
     }
 }
 
+// Unit quaternion of the field term at every site from B [3][N] (double):
+// (cos phi, sin phi B/|B|), phi = mu |B| dt, i.e. U(x) = exp(-i mu dt
+// sigma.B(x)) (Sec. 5, Eq. sigmaB_comm); the identity where B = 0.
+// Non-finite input sets FLAG_NONFINITE.
+__device__ __forceinline__ void store_quat(float4 *p, double w, double x, double y, double z)
+{
+    *p = make_float4((float)w, (float)x, (float)y, (float)z);
+}
+__device__ __forceinline__ void store_quat(DQuad *p, double w, double x, double y, double z)
+{
+    p->a = make_double2(w, x);
+    p->b = make_double2(y, z);
+}
+
+template <class V>
+__global__ void __launch_bounds__(256)
+k_field_quaternions(const double *__restrict__ B, int64_t N, double mu_dt, V *__restrict__ out,
+                    unsigned *__restrict__ flags)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const double bx = B[s], by = B[N + s], bz = B[2 * N + s];
+    const double nb = sqrt(bx * bx + by * by + bz * bz);
+    double w = 1.0, x = 0.0, y = 0.0, z = 0.0;
+    if (!(nb < 1e300)) {
+        atomicOr(flags, (unsigned)FLAG_NONFINITE);
+    } else if (nb > 0.0) {
+        double sn, cs;
+        sincos(mu_dt * nb, &sn, &cs);
+        const double f = sn / nb;
+        w = cs;
+        x = f * bx;
+        y = f * by;
+        z = f * bz;
+    }
+    store_quat(out + s, w, x, y, z);
+}
+
 cudaError_t launch_conserved_final(qlbm_ctx *h)
 {
     k_conserved_final<<<1, kRedBlock, 0, h->stream>>>(h->partials, h->nred, h->hc.xi, h->g.N,
@@ -294,6 +332,7 @@ void qlbm_destroy(qlbm_handle h)
     if (h->dtau_acc) cudaFree(h->dtau_acc);
     if (h->scratch_state) cudaFree(h->scratch_state);
     if (h->fd_fail) cudaFree(h->fd_fail);
+    if (h->qfield) cudaFree(h->qfield);
     if (h->neg_count) cudaFree(h->neg_count);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     free_rollout(h);
@@ -710,6 +749,51 @@ int qlbm_set_magnetic_field(qlbm_handle h, double mu, const double B[3])
     for (int i = 0; i < 9; ++i) h->rot[i] = rot[i];
     h->mag = mag;
     if (h->graph) {   // the captured launches carry the old field
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->ro_steps = -1;
+    return QLBM_OK;
+}
+
+int qlbm_set_magnetic_field_array(qlbm_handle h, double mu, const double *B, int ptr_kind)
+{
+    if (!valid(h) || !B) return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_magnetic_field_array: bad argument");
+    if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
+    if (!(mu == mu) || !(fabs(mu) < 1e300))
+        return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_magnetic_field_array: mu must be finite");
+    if (h->prec == QLBM_DF64 || h->prec == QLBM_FP64_DF)
+        return fail(h, QLBM_ERR_UNSUPPORTED,
+                    "qlbm_set_magnetic_field_array: a per-site field needs QLBM_FP64, QLBM_FP32 or QLBM_FP16_DEV storage");
+    const int64_t N = h->g.N;
+    const bool dbl = h->prec == QLBM_FP64;
+    const size_t vb = dbl ? sizeof(DQuad) : sizeof(float4);
+    if (!h->qfield) CK(h, cudaMalloc(&h->qfield, (size_t)N * vb));
+    const double *src = B;
+    if (ptr_kind == QLBM_HOST) {
+        int rc = ensure_staging(h, 3 * (size_t)N * sizeof(double));
+        if (rc) return rc;
+        CK(h, cudaMemcpyAsync(h->staging, B, 3 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        src = h->staging;
+    }
+    // earlier steps' flags are reported first, so that a bad field is not
+    // mistaken for them
+    CK(h, cudaStreamSynchronize(h->stream));
+    int rc = check_flags(h);
+    if (rc) return rc;
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    if (dbl)
+        k_field_quaternions<<<nb, 256, 0, h->stream>>>(src, N, mu * h->dt, static_cast<DQuad *>(h->qfield), h->flags);
+    else
+        k_field_quaternions<<<nb, 256, 0, h->stream>>>(src, N, mu * h->dt, static_cast<float4 *>(h->qfield), h->flags);
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (check_flags(h) != QLBM_OK) {
+        h->mag = FIELD_NONE;
+        return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_magnetic_field_array: non-finite field value (field switched off)");
+    }
+    h->mag = FIELD_SITE;
+    if (h->graph) {   // the captured launches carry the previous field variant
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
     }

@@ -222,7 +222,7 @@ __device__ __forceinline__ unsigned collide_fd(double *f, double *sx, double *sy
     return flag;
 }
 
-template <int D, bool ODD>
+template <int D, bool ODD, int FIELD>
 __global__ void __launch_bounds__(kStepBlock)
 k_step_aa_fd(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<double> k, FdArgs a,
              unsigned *__restrict__ flags)
@@ -234,6 +234,7 @@ k_step_aa_fd(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<double> k, FdA
     double f[Q], sx[Q], sy[Q], sz[Q];
     gather<D, CodecF64, ODD>(pl, g, si, codec, f, sx, sy, sz);
     const unsigned flag = collide_fd<D>(f, sx, sy, sz, k, a);
+    apply_field<D, FIELD, double>(sx, sy, sz, k, si.s);
     SiteIdx so = si;
     so.s += g.zero;
     so.x += g.zero;
@@ -252,7 +253,7 @@ k_step_aa_fd(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<double> k, FdA
 // collision leaves unchanged) go through the single-precision solve
 // (fd_params_site_f; double near degenerate eigenvalues).  The solve runs
 // while the stores drain.  Outputs float [N] (axis [3][N]).
-template <int D, class Codec, bool ODD, bool MAG>
+template <int D, class Codec, bool ODD, int FIELD>
 __global__ void __launch_bounds__(kStepBlock, step_min_blocks<D, Codec>())
 k_step_aa_fdout(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<float> k, Codec codec,
                 float beta0, unsigned *__restrict__ flags, float *__restrict__ beta, float *__restrict__ mu_up,
@@ -265,7 +266,7 @@ k_step_aa_fdout(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<
     gather<D, Codec, ODD>(pl, g, si, codec, f, sx, sy, sz);
     float mom[5];
     const unsigned flag = collide_dev<D, true>(f, sx, sy, sz, k, mom);
-    if constexpr (MAG) rotate_spins<D, float>(sx, sy, sz, k.rot);
+    apply_field<D, FIELD, float>(sx, sy, sz, k, si.s);
     SiteIdx so = si;
     so.s += g.zero;
     so.x += g.zero;

@@ -63,7 +63,8 @@ struct qlbm_ctx {
     cudaGraphExec_t graph = nullptr;
     int use_graph = 1;
     int eq_path = 0;                    // QLBM_EQ_DIRECT or QLBM_EQ_FD_PARAMS
-    int mag = 0;                        // magnetic-field term enabled
+    int mag = 0;                        // magnetic-field term: FIELD_NONE, FIELD_UNIFORM or FIELD_SITE
+    void *qfield = nullptr;             // per-site field: N unit quaternions (float4, or DQuad for FP64)
     double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};   // its per-step spin rotation
     unsigned long long *fd_fail = nullptr;   // device counter of unresolved sites
     unsigned long long *neg_count = nullptr; // device counter of the negative-equilibrium diagnostic

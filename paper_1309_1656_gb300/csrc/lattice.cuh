@@ -38,6 +38,14 @@ template <int D> __host__ __device__ constexpr int cnorm2(int q)
 }
 template <int D> __host__ __device__ constexpr int opposite(int q) { return Lattice<D>::Q - 1 - q; }
 
+// Per-site field of the magnetic-field term: one unit quaternion per site,
+// float4 for single-precision arithmetic, two double2 (DQuad) otherwise.
+struct __align__(16) DQuad {
+    double2 a, b;
+};
+template <typename R> struct FieldOf { using V = DQuad; };
+template <> struct FieldOf<float> { using V = float4; };
+
 // Per-handle collision constants in the kernel's arithmetic type.  With
 // j = J/n in lattice units (u = xi j) and K = beta0 xi^2 / 2:
 //   beta0 eps = K (E2/n - |j|^2),            E2 = sum_i |i|^2 f_i,
@@ -54,7 +62,8 @@ template <typename R> struct Coll {
     R w[3];         // weights for |i|^2 = 0, 1, 2
     R g00, g01, g11, gj;
     R S2;           // sum_i w_i |i|^2 (= c / K)
-    R rot[9];       // spin rotation of the magnetic-field term (row-major), if enabled
+    R rot[9];       // spin rotation of a uniform magnetic field (row-major), if enabled
+    const typename FieldOf<R>::V *qf;   // per-site field: unit quaternion of site s at qf[s], if enabled
 };
 
 // Magnetic-field term (Sec. 5): the Vlasov commutator -i[mu sigma.B, W]
@@ -62,6 +71,12 @@ template <typename R> struct Coll {
 // U = exp(-i mu dt sigma.B), i.e. every Bloch vector s_i is rotated by
 // 2 mu |B| dt about B (ds/dt = 2 mu B x s).  It commutes with the
 // SU(2)-covariant collision, so applying it after the BGK update is exact.
+// FIELD selects the kernels' variant: none, one field for the whole
+// lattice (rotation matrix in Coll::rot), or a field B(x) per site (the
+// rotation of site x from the unit quaternion (cos phi, sin phi B/|B|),
+// phi = mu |B(x)| dt, which the library derives from B when it is set).
+enum : int { FIELD_NONE = 0, FIELD_UNIFORM = 1, FIELD_SITE = 2 };
+
 template <int D, typename R>
 __device__ __forceinline__ void rotate_spins(R *sx, R *sy, R *sz, const R (&rot)[9])
 {
@@ -72,6 +87,66 @@ __device__ __forceinline__ void rotate_spins(R *sx, R *sy, R *sz, const R (&rot)
         sx[q] = rot[0] * x + rot[1] * y + rot[2] * z;
         sy[q] = rot[3] * x + rot[4] * y + rot[5] * z;
         sz[q] = rot[6] * x + rot[7] * y + rot[8] * z;
+    }
+}
+
+// Rotation matrix of the unit quaternion (w, x, y, z): the rotation by
+// 2 acos(w) about (x, y, z).
+template <typename R>
+__device__ __forceinline__ void quat_rotation(R w, R x, R y, R z, R (&rot)[9])
+{
+    const R xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+    const R wx = w * x, wy = w * y, wz = w * z;
+    rot[0] = R(1) - R(2) * (yy + zz);
+    rot[1] = R(2) * (xy - wz);
+    rot[2] = R(2) * (xz + wy);
+    rot[3] = R(2) * (xy + wz);
+    rot[4] = R(1) - R(2) * (xx + zz);
+    rot[5] = R(2) * (yz - wx);
+    rot[6] = R(2) * (xz - wy);
+    rot[7] = R(2) * (yz + wx);
+    rot[8] = R(1) - R(2) * (xx + yy);
+}
+__device__ __forceinline__ void load_quat(const float4 *p, float &w, float &x, float &y, float &z)
+{
+    const float4 v = *p;
+    w = v.x;
+    x = v.y;
+    y = v.z;
+    z = v.w;
+}
+__device__ __forceinline__ void load_quat(const DQuad *p, double &w, double &x, double &y, double &z)
+{
+    const double2 a = p->a, b = p->b;
+    w = a.x;
+    x = a.y;
+    y = b.x;
+    z = b.y;
+}
+
+// The spin rotation of the field term at site s: the uniform matrix, or the
+// site's own from its quaternion.
+template <int FIELD, typename R>
+__device__ __forceinline__ void field_rotation(const Coll<R> &k, int s, R (&rot)[9])
+{
+    if constexpr (FIELD == FIELD_SITE) {
+        R w, x, y, z;
+        load_quat(k.qf + s, w, x, y, z);
+        quat_rotation(w, x, y, z, rot);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) rot[i] = k.rot[i];
+    }
+}
+
+// The field term applied to the post-collision spins of site s.
+template <int D, int FIELD, typename R>
+__device__ __forceinline__ void apply_field(R *sx, R *sy, R *sz, const Coll<R> &k, int s)
+{
+    if constexpr (FIELD != FIELD_NONE) {
+        R rot[9];
+        field_rotation<FIELD>(k, s, rot);
+        rotate_spins<D, R>(sx, sy, sz, rot);
     }
 }
 // Bits of the device flag word.
@@ -275,9 +350,6 @@ __device__ __forceinline__ unsigned collide_dev(float *d, float *sx, float *sy, 
 // precision (float4, one 128-bit access per thread), 256 B in half (4
 // halves, one 64-bit access), 1 KB in double (two 128-bit accesses).  A
 // neighbour shift moves by whole vectors, so every access stays aligned.
-struct __align__(16) DQuad {
-    double2 a, b;
-};
 template <class T> struct QuadOf;
 template <> struct QuadOf<double> { using V = DQuad; };
 template <> struct QuadOf<float> { using V = float4; };

@@ -3,6 +3,8 @@
 // kernels_<lattice>_<codec>.cu instantiates one of them.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 #include "adjoint.cuh"
 #include "fdkernels.cuh"
@@ -38,7 +40,20 @@ template <typename R> Coll<R> make_coll(const qlbm_ctx *h)
     c.gj = (R)(1.0 / sx2);
     c.S2 = (R)S2;
     for (int i = 0; i < 9; ++i) c.rot[i] = (R)h->rot[i];
+    c.qf = static_cast<const typename FieldOf<R>::V *>(h->qfield);
     return c;
+}
+
+// Calls f(std::integral_constant<int, FIELD>{}) for the handle's field mode
+// (FIELD_NONE, FIELD_UNIFORM or FIELD_SITE), so that a launcher names each
+// kernel once for all three variants.
+template <class F> inline cudaError_t with_field(int mode, F &&f)
+{
+    switch (mode) {
+    case FIELD_UNIFORM: return f(std::integral_constant<int, FIELD_UNIFORM>{});
+    case FIELD_SITE: return f(std::integral_constant<int, FIELD_SITE>{});
+    default: return f(std::integral_constant<int, FIELD_NONE>{});
+    }
 }
 
 inline InitConsts make_init(const qlbm_ctx *h)
@@ -120,27 +135,23 @@ template <int D, class Codec> struct Launchers {
             const int rpb = step_rows_per_block(h->g, D == 2 ? 8 : 4, step_min_blocks<D, Codec>(), h->sms);
             const dim3 grr = row_group_grid(h->g, rpb);
             const size_t sm = rows_smem_bytes<D, Codec>((int)blk.x);
-            if (h->mag) {
+            return with_field(h->mag, [&](auto fc) {
+                constexpr int F = decltype(fc)::value;
                 if (odd)
-                    k_step_aa_rows<D, Codec, true, true><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
+                    k_step_aa_rows<D, Codec, true, F><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
                 else
-                    k_step_aa_rows<D, Codec, false, true><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
-            } else {
-                if (odd)
-                    k_step_aa_rows<D, Codec, true><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
-                else
-                    k_step_aa_rows<D, Codec, false><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
-            }
-        } else if (h->mag) {
-            if (odd)
-                k_step_aa<D, Codec, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-            else
-                k_step_aa<D, Codec, false, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+                    k_step_aa_rows<D, Codec, false, F><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
+                return cudaGetLastError();
+            });
         } else {
-            if (odd)
-                k_step_aa<D, Codec, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-            else
-                k_step_aa<D, Codec, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+            return with_field(h->mag, [&](auto fc) {
+                constexpr int F = decltype(fc)::value;
+                if (odd)
+                    k_step_aa<D, Codec, true, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+                else
+                    k_step_aa<D, Codec, false, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+                return cudaGetLastError();
+            });
         }
         return cudaGetLastError();
     }
@@ -199,28 +210,24 @@ template <int D, class Codec> struct Launchers {
     static cudaError_t adjoint(qlbm_ctx *h, const void *state, const void *lam_in, void *lam_out)
     {
         const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
-        if (h->mag)
-            k_adjoint<D, Codec, true><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, state), planes_of<R>(h, lam_in),
-                                                                  planes_of<R>(h, lam_out), h->g, make_coll<R>(h),
-                                                                  make_codec<Codec>(h), h->dtau_acc);
-        else
-            k_adjoint<D, Codec, false><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, state), planes_of<R>(h, lam_in),
-                                                                   planes_of<R>(h, lam_out), h->g, make_coll<R>(h),
-                                                                   make_codec<Codec>(h), h->dtau_acc);
-        return cudaGetLastError();
+        return with_field(h->mag, [&](auto fc) {
+            constexpr int F = decltype(fc)::value;
+            k_adjoint<D, Codec, F><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, state), planes_of<R>(h, lam_in),
+                                                               planes_of<R>(h, lam_out), h->g, make_coll<R>(h),
+                                                               make_codec<Codec>(h), h->dtau_acc);
+            return cudaGetLastError();
+        });
     }
 
     static cudaError_t push(qlbm_ctx *h, const void *src, void *dst)
     {
         const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
-        if (h->mag)
-            k_step_push<D, Codec, true><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, src), planes_of<S>(h, dst), h->g,
-                                                                    make_coll<R>(h), make_codec<Codec>(h), h->flags);
-        else
-            k_step_push<D, Codec, false><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, src), planes_of<S>(h, dst),
-                                                                     h->g, make_coll<R>(h), make_codec<Codec>(h),
-                                                                     h->flags);
-        return cudaGetLastError();
+        return with_field(h->mag, [&](auto fc) {
+            constexpr int F = decltype(fc)::value;
+            k_step_push<D, Codec, F><<<grd, blk, 0, h->stream>>>(planes_of<S>(h, src), planes_of<S>(h, dst), h->g,
+                                                                 make_coll<R>(h), make_codec<Codec>(h), h->flags);
+            return cudaGetLastError();
+        });
     }
 
     static cudaError_t copy_natural(qlbm_ctx *h, void *dst)
@@ -275,11 +282,16 @@ template <int D, class Codec> struct Launchers {
         if constexpr (std::is_same<Codec, CodecF64>::value) {
             const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
             const FdArgs a{h->hc.beta0, h->hc.xi};
-            if (odd)
-                k_step_aa_fd<D, true><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_coll<double>(h), a, h->flags);
-            else
-                k_step_aa_fd<D, false><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_coll<double>(h), a, h->flags);
-            return cudaGetLastError();
+            return with_field(h->mag, [&](auto fc) {
+                constexpr int F = decltype(fc)::value;
+                if (odd)
+                    k_step_aa_fd<D, true, F><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_coll<double>(h), a,
+                                                                         h->flags);
+                else
+                    k_step_aa_fd<D, false, F><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_coll<double>(h), a,
+                                                                          h->flags);
+                return cudaGetLastError();
+            });
         } else {
             return cudaErrorNotSupported;
         }
@@ -316,18 +328,18 @@ template <int D, class Codec> struct Launchers {
             const Coll<R> k = make_coll<R>(h);
             const Codec codec = make_codec<Codec>(h);
             const float b0 = (float)h->hc.beta0;
-#define QLBM_FDOUT(ODD, MAG)                                                                                   \
-    k_step_aa_fdout<D, Codec, ODD, MAG><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, b0, h->flags, beta, mu_up, \
-                                                                    mu_dn, axis, h->fd_fail)
-            if (h->mag) {
-                if (odd) QLBM_FDOUT(true, true);
-                else QLBM_FDOUT(false, true);
-            } else {
-                if (odd) QLBM_FDOUT(true, false);
-                else QLBM_FDOUT(false, false);
-            }
-#undef QLBM_FDOUT
-            return cudaGetLastError();
+            return with_field(h->mag, [&](auto fc) {
+                constexpr int F = decltype(fc)::value;
+                if (odd)
+                    k_step_aa_fdout<D, Codec, true, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, b0, h->flags,
+                                                                                   beta, mu_up, mu_dn, axis,
+                                                                                   h->fd_fail);
+                else
+                    k_step_aa_fdout<D, Codec, false, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, b0, h->flags,
+                                                                                    beta, mu_up, mu_dn, axis,
+                                                                                    h->fd_fail);
+                return cudaGetLastError();
+            });
         } else {
             return cudaErrorNotSupported;
         }

@@ -86,7 +86,7 @@ template <int D, class Codec> constexpr int step_min_blocks()
 
 // One AA step (even: ODD = false, odd: ODD = true), fused
 // moments + equilibrium + collision + streaming.
-template <int D, class Codec, bool ODD, bool MAG = false>
+template <int D, class Codec, bool ODD, int FIELD = FIELD_NONE>
 __global__ void __launch_bounds__(kStepBlock, step_min_blocks<D, Codec>())
 k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typename Codec::R> k,
           Codec codec, unsigned *__restrict__ flags)
@@ -98,7 +98,7 @@ k_step_aa(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typena
     R f[Q], sx[Q], sy[Q], sz[Q];
     gather<D, Codec, ODD>(pl, g, si, codec, f, sx, sy, sz);
     const unsigned flag = Codec::template collide<D>(f, sx, sy, sz, k);
-    if constexpr (MAG) rotate_spins<D, R>(sx, sy, sz, k.rot);
+    apply_field<D, FIELD, R>(sx, sy, sz, k, si.s);
     // g.zero is 0 at run time; adding it keeps the compiler from carrying the
     // 4b load addresses (identical to the store addresses) through the
     // collision in registers.
@@ -183,7 +183,7 @@ template <int D, class Codec> constexpr size_t rows_smem_bytes(int block)
 // block barrier is needed.  Each location is read and written by exactly
 // one site update per step, so the early loads of row r + 1 never meet the
 // stores of row r.
-template <int D, class Codec, bool ODD, bool MAG = false>
+template <int D, class Codec, bool ODD, int FIELD = FIELD_NONE>
 __global__ void __launch_bounds__(kStepBlock, step_min_blocks<D, Codec>())
 k_step_aa_rows(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<typename Codec::R> k,
                Codec codec, int rpb, unsigned *__restrict__ flags)
@@ -215,7 +215,7 @@ k_step_aa_rows(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<t
             codec.decode4(cur[q * bw], f[p], sx[p], sy[p], sz[p]);
         }
         flag |= Codec::template collide<D>(f, sx, sy, sz, k);
-        if constexpr (MAG) rotate_spins<D, R>(sx, sy, sz, k.rot);
+        apply_field<D, FIELD, R>(sx, sy, sz, k, row * g.nx + x);
         // store addresses recomputed from g.zero (see k_step_aa)
         const SiteIdx so = site_at(g, x + g.zero, row);
 #pragma unroll

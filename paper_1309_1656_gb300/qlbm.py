@@ -81,6 +81,7 @@ _fd_params_adjoint = _sig("qlbm_fd_params_adjoint", _i, [_vp, _vp, _vp, _vp, _vp
 _step_fd_output = _sig("qlbm_step_fd_output", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64), _i])
 _init_fd = _sig("qlbm_init_fd_params", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _i])
 _set_field = _sig("qlbm_set_magnetic_field", _i, [_vp, _d, ctypes.POINTER(_d)])
+_set_field_array = _sig("qlbm_set_magnetic_field_array", _i, [_vp, _d, _vp, _i])
 _set_eq_path = _sig("qlbm_set_equilibrium_path", _i, [_vp, _i])
 _conserved_static = _sig("qlbm_conserved_static", _i, [_i, ctypes.POINTER(_i64), _d, _vp, _vp, _vp])
 _negative_eq = _sig("qlbm_negative_eq_count", _i, [_vp, ctypes.POINTER(_i64), _vp, _i])
@@ -373,6 +374,13 @@ def qlbm_set_magnetic_field(h, mu, B):
     _check(_set_field(h, float(mu), b), h)
 
 
+def qlbm_set_magnetic_field_array(h, mu, B):
+    """Per-site magnetic field B [3][N] (numpy float64 or CUDA float64 tensor)."""
+    d, b, N, dev = _geom(h)
+    p, k = _ptr(B, 3 * N, dev)
+    _check(_set_field_array(h, float(mu), p, k), h)
+
+
 def qlbm_set_equilibrium_path(h, path):
     _check(_set_eq_path(h, int(path)), h)
 
@@ -542,6 +550,10 @@ class Lattice:
 
     def set_magnetic_field(self, mu, B):
         qlbm_set_magnetic_field(self.h, mu, B)
+
+    def set_magnetic_field_array(self, mu, B):
+        qlbm_set_magnetic_field_array(self.h, mu, np.ascontiguousarray(B, dtype=np.float64)
+                                      if isinstance(B, np.ndarray) else B)
 
     def set_equilibrium_path(self, path):
         qlbm_set_equilibrium_path(self.h, path)
