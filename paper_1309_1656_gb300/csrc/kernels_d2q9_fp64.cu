@@ -1,9 +1,11 @@
 // D2Q9 (Sec. 3.1, d = 2, b = 9) kernels for FP64 storage: the dispatch tables of FP64 storage with the
 // FP64 and the double-float step, in a translation unit of its own so the instantiations
 // compile in parallel.
-#include "launch.cuh"
+#include "steplaunch.cuh"
 
 namespace qlbm {
+template cudaError_t Launchers<2, CodecF64>::step(qlbm_ctx *, bool);
+template cudaError_t Launchers<2, CodecF64>::step_fd(qlbm_ctx *, bool);
 const LatticeOps *ops_d2q9_fp64() { return Launchers<2, CodecF64>::table(); }
 
 // FP64 storage with the double-float step: the FP64 operations, the step of

@@ -1,0 +1,8 @@
+// D3Q19 (Sec. 3.1, d = 3, b = 19) fused step launcher for FP16 deviation storage, compiled apart
+// from the rest of its dispatch table (kernels_d3q19_fp16.cu) so that the heaviest
+// kernels build in parallel.
+#include "steplaunch.cuh"
+
+namespace qlbm {
+template cudaError_t Launchers<3, CodecF16Dev>::step(qlbm_ctx *, bool);
+}  // namespace qlbm

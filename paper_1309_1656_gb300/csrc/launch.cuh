@@ -111,50 +111,12 @@ template <int D, class Codec> struct Launchers {
     }
     static Planes<S, Q> planes(const qlbm_ctx *h) { return planes_of<S>(h, h->pop); }
 
-    static cudaError_t step(qlbm_ctx *h, bool odd)
-    {
-        const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
-        const Planes<S, Q> pl = planes(h);
-        const Coll<R> k = make_coll<R>(h);
-        const Codec codec = make_codec<Codec>(h);
-        if constexpr (TwoPass<Codec>::value) {
-            if (h->mag) {
-                if (odd)
-                    k_step_aa_df2<D, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-                else
-                    k_step_aa_df2<D, false, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-            } else {
-                if (odd)
-                    k_step_aa_df2<D, true, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-                else
-                    k_step_aa_df2<D, false, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-            }
-        } else if constexpr (RowPipelined<Codec>::value) {
-            // rows per block from a sweep on GB300 (FP16): D2Q9 4096^2 gains
-            // 14 % at 8, D3Q19 192^3 - 256^3 4-7 % at 4 (more rows lose to the tail)
-            const int rpb = step_rows_per_block(h->g, D == 2 ? 8 : 4, step_min_blocks<D, Codec>(), h->sms);
-            const dim3 grr = row_group_grid(h->g, rpb);
-            const size_t sm = rows_smem_bytes<D, Codec>((int)blk.x);
-            return with_field(h->mag, [&](auto fc) {
-                constexpr int F = decltype(fc)::value;
-                if (odd)
-                    k_step_aa_rows<D, Codec, true, F><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
-                else
-                    k_step_aa_rows<D, Codec, false, F><<<grr, blk, sm, h->stream>>>(pl, h->g, k, codec, rpb, h->flags);
-                return cudaGetLastError();
-            });
-        } else {
-            return with_field(h->mag, [&](auto fc) {
-                constexpr int F = decltype(fc)::value;
-                if (odd)
-                    k_step_aa<D, Codec, true, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-                else
-                    k_step_aa<D, Codec, false, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-                return cudaGetLastError();
-            });
-        }
-        return cudaGetLastError();
-    }
+    // The step launchers (steplaunch.cuh) are compiled in translation units
+    // of their own (kernels_<lattice>_<codec>_step.cu), in parallel with the
+    // rest of the table.
+    static cudaError_t step(qlbm_ctx *h, bool odd);
+    static cudaError_t step_fd(qlbm_ctx *h, bool odd);
+    static cudaError_t step_fdout(qlbm_ctx *h, bool odd, float *beta, float *mu_up, float *mu_dn, float *axis);
 
     static cudaError_t init_eq(qlbm_ctx *h, const double *rho4, const double *u, const double *eps)
     {
@@ -277,26 +239,6 @@ template <int D, class Codec> struct Launchers {
         return cudaGetLastError();
     }
 
-    static cudaError_t step_fd(qlbm_ctx *h, bool odd)
-    {
-        if constexpr (std::is_same<Codec, CodecF64>::value) {
-            const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
-            const FdArgs a{h->hc.beta0, h->hc.xi};
-            return with_field(h->mag, [&](auto fc) {
-                constexpr int F = decltype(fc)::value;
-                if (odd)
-                    k_step_aa_fd<D, true, F><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_coll<double>(h), a,
-                                                                         h->flags);
-                else
-                    k_step_aa_fd<D, false, F><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_coll<double>(h), a,
-                                                                          h->flags);
-                return cudaGetLastError();
-            });
-        } else {
-            return cudaErrorNotSupported;
-        }
-    }
-
     static cudaError_t fd_params_adjoint(qlbm_ctx *h, const double *gbeta, const double *gmu_up,
                                          const double *gmu_dn, const double *gaxis, double *lam)
     {
@@ -320,31 +262,6 @@ template <int D, class Codec> struct Launchers {
         return cudaGetLastError();
     }
 
-    static cudaError_t step_fdout(qlbm_ctx *h, bool odd, float *beta, float *mu_up, float *mu_dn, float *axis)
-    {
-        if constexpr (Codec::DEV) {
-            const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
-            const Planes<S, Q> pl = planes(h);
-            const Coll<R> k = make_coll<R>(h);
-            const Codec codec = make_codec<Codec>(h);
-            const float b0 = (float)h->hc.beta0;
-            return with_field(h->mag, [&](auto fc) {
-                constexpr int F = decltype(fc)::value;
-                if (odd)
-                    k_step_aa_fdout<D, Codec, true, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, b0, h->flags,
-                                                                                   beta, mu_up, mu_dn, axis,
-                                                                                   h->fd_fail);
-                else
-                    k_step_aa_fdout<D, Codec, false, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, b0, h->flags,
-                                                                                    beta, mu_up, mu_dn, axis,
-                                                                                    h->fd_fail);
-                return cudaGetLastError();
-            });
-        } else {
-            return cudaErrorNotSupported;
-        }
-    }
-
     static cudaError_t negative_eq(qlbm_ctx *h, unsigned long long *count, unsigned *mask)
     {
         const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
@@ -355,6 +272,19 @@ template <int D, class Codec> struct Launchers {
             k_negative_eq<D, Codec, false><<<grd, blk, 0, h->stream>>>(planes(h), h->g, make_codec<Codec>(h),
                                                                        make_init(h), count, mask);
         return cudaGetLastError();
+    }
+
+    // Entries that exist for some codecs only: named inside if constexpr, so
+    // that the others never reference (and never need) their definitions.
+    static constexpr auto step_fd_entry()
+    {
+        if constexpr (std::is_same<Codec, CodecF64>::value) return &step_fd;
+        else return static_cast<decltype(&step_fd)>(nullptr);
+    }
+    static constexpr auto step_fdout_entry()
+    {
+        if constexpr (Codec::DEV) return &step_fdout;
+        else return static_cast<decltype(&step_fdout)>(nullptr);
     }
 
     // The reverse mode (adjoint, push, cotangent import/export) exists for
@@ -370,10 +300,8 @@ template <int D, class Codec> struct Launchers {
         } else {
             static const LatticeOps t = {&step,    &init_eq,      &get_state,  &set_state,  &moments,
                                          &conserved_partial, &adjoint, &push, &copy_natural, &lam_import,
-                                         &lam_export, &init_adjoint, &fd_params,
-                                         std::is_same<Codec, CodecF64>::value ? &step_fd : nullptr,
-                                         &fd_params_adjoint, &init_fd, Codec::DEV ? &step_fdout : nullptr,
-                                         &negative_eq};
+                                         &lam_export, &init_adjoint, &fd_params, step_fd_entry(),
+                                         &fd_params_adjoint, &init_fd, step_fdout_entry(), &negative_eq};
             return &t;
         }
     }
