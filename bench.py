@@ -114,7 +114,7 @@ def recorded_traffic(kernel_key):
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel_key)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(tuple(e.get("hashed_files", STEP_KERNEL_SOURCES))):
         return None
     return float(e["dram_bytes_per_site"])
 

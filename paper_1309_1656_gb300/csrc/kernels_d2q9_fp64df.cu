@@ -8,15 +8,19 @@ namespace qlbm {
 
 template <int D> cudaError_t step_f64df(qlbm_ctx *h, bool odd)
 {
-    const dim3 blk = site_block(h->g), grd = site_grid(h->g, blk.x);
+    // blocks of two warps over F64dfSplit<D>::SITES consecutive sites of a
+    // row, so the grid is laid out for that block width
+    Grid g = h->g;
+    g.nxb = (g.nx + F64dfSplit<D>::SITES - 1) / F64dfSplit<D>::SITES;
+    const dim3 blk(kF64dfBlock), grd((unsigned)((int64_t)g.nxb * g.ny * g.nz));
     const Planes<double, Lattice<D>::Q> pl = Launchers<D, CodecF64>::planes(h);
     const Coll<df> k = make_coll<df>(h);
     if (h->mag) {
-        if (odd) k_step_aa_f64df<D, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, h->flags);
-        else k_step_aa_f64df<D, false, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, h->flags);
+        if (odd) k_step_aa_f64df<D, true, true><<<grd, blk, 0, h->stream>>>(pl, g, k, h->flags);
+        else k_step_aa_f64df<D, false, true><<<grd, blk, 0, h->stream>>>(pl, g, k, h->flags);
     } else {
-        if (odd) k_step_aa_f64df<D, true, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, h->flags);
-        else k_step_aa_f64df<D, false, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, h->flags);
+        if (odd) k_step_aa_f64df<D, true, false><<<grd, blk, 0, h->stream>>>(pl, g, k, h->flags);
+        else k_step_aa_f64df<D, false, false><<<grd, blk, 0, h->stream>>>(pl, g, k, h->flags);
     }
     return cudaGetLastError();
 }
