@@ -2,10 +2,11 @@
 // values of a site takes the whole register file of a thread (255 registers,
 // 8 warps per SM), and with so few warps the loads and the long arithmetic
 // do not overlap.  This kernel streams the populations through the moment
-// sums (pass 1), keeping only their hi parts (4b floats), forms the
-// coefficients, then re-reads the lo parts of each direction together with
-// its opposite (pass 2: a quarter of the state's bytes, cache hits),
-// updates the pair and stores it.  In the AA pattern the read locations of a direction
+// sums (pass 1), keeping their hi parts (4b floats) in registers and their
+// lo parts in shared memory (4b x 4 B per thread: 38.9 KB per D3Q19 block),
+// forms the coefficients, then takes the lo parts of each direction
+// together with its opposite back from shared memory (pass 2), updates the
+// pair and stores it.  Every value is read from HBM once.  In the AA pattern the read locations of a direction
 // and of its opposite are exactly the pair's two write locations (even step:
 // slots q and opposite(q) at x; odd step: slot opposite(q) at x - e_q and
 // slot q at x + e_q), so updating pair by pair in place is race-free within
@@ -54,9 +55,12 @@ __global__ void __launch_bounds__(kStepBlock, TwoPass<CodecDF>::min_blocks<D>())
 k_step_aa_df2(const Planes<df, Lattice<D>::Q> pl, Grid g, Coll<df> k, CodecDF codec, unsigned *__restrict__ flags)
 {
     constexpr int Q = Lattice<D>::Q;
+    // lo parts, kept from pass 1 in shared memory (a thread reads back only
+    // what it wrote: no barrier)
+    __shared__ float4 lo_stage[Q][kStepBlock];
     SiteIdx si;
     if (!site_of_block(g, si)) return;
-    float hf[Q], hx[Q], hy[Q], hz[Q];   // hi parts, kept from pass 1
+    float hf[Q], hx[Q], hy[Q], hz[Q];   // hi parts, kept from pass 1 in registers
     DFSums a;
     a.zero();
 #pragma unroll
@@ -67,6 +71,7 @@ k_step_aa_df2(const Planes<df, Lattice<D>::Q> pl, Grid g, Coll<df> k, CodecDF co
         hx[p] = h.y;
         hy[p] = h.z;
         hz[p] = h.w;
+        lo_stage[p][threadIdx.x] = l;
         df_accumulate<D>(a, p, df(h.x, l.x), df(h.y, l.y), df(h.z, l.z), df(h.w, l.w));
     }
     const DFCoef c = df_coefficients<D>(a, k);
@@ -78,11 +83,13 @@ k_step_aa_df2(const Planes<df, Lattice<D>::Q> pl, Grid g, Coll<df> k, CodecDF co
 #pragma unroll
     for (int q = 0; q <= (Q - 1) / 2; ++q) {
         const int qb = Q - 1 - q;
-        const float4 l = pl.p[read_slot<D, ODD>(q)][read_site<D, ODD>(g, s2, q) + codec.lo];
+        // (index through g.zero: the compiler re-reads shared memory instead
+        // of keeping pass 1's lo values in registers)
+        const float4 l = lo_stage[q][threadIdx.x + g.zero];
         df f(hf[q], l.x), x(hx[q], l.y), y(hy[q], l.z), z(hz[q], l.w);
         df fb, xb, yb, zb;
         if (qb != q) {
-            const float4 lb = pl.p[read_slot<D, ODD>(qb)][read_site<D, ODD>(g, s2, qb) + codec.lo];
+            const float4 lb = lo_stage[qb][threadIdx.x + g.zero];
             fb = df(hf[qb], lb.x);
             xb = df(hx[qb], lb.y);
             yb = df(hy[qb], lb.z);
