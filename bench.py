@@ -230,8 +230,8 @@ def job_mlups(ws, sites_per_rank, steps, seconds):
 STEP_KERNEL = {"fp32": "k_step_aa<%d, CodecF32>", "fp16dev": "k_step_aa_rows<%d, CodecF16Dev>",
                "fp64": "k_step_aa<%d, CodecF64>", "fp64df": "k_step_aa_f64df<%d>", "df64": "k_step_aa_df2<%d>"}
 STEP_LIMIT = {"fp64": "alu: the FP64 pipe (GB300 issues double arithmetic at 1/64 of the float rate)",
-              "fp64df": "alu: FP64 pipe (pass-1 moment sums, rounding back to double) and integer pipe "
-                        "(double -> double-float splits)"}
+              "fp64df": "issue: instruction-issue bound (integer splits of the doubles and widening for the "
+                        "rounding back, double-float sums and update on the FP32 pipes, one FP64 addition per value)"}
 
 
 class Bench:

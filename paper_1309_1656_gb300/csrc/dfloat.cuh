@@ -192,15 +192,18 @@ struct DFCoef {
     unsigned flag;
 };
 
-template <int D> __device__ __forceinline__ DFCoef df_coefficients(const DFSums &a, const Coll<df> &k)
+// Per-site coefficients from the moment sums n, S, J = sum_i i f_i and
+// E = sum_i |i|^2 f_i (lattice units).
+template <int D>
+__device__ __forceinline__ DFCoef df_coefficients_of(df n, df Sx, df Sy, df Sz, df Jx, df Jy, df Jz, df E,
+                                                     const Coll<df> &k)
 {
     DFCoef c;
-    const df n = a.n.value(), Sx = a.Sx.value(), Sy = a.Sy.value(), Sz = a.Sz.value();
     const df rn = recip(n);
-    c.jx = (a.jxp.value() - a.jxm.value()) * rn;
-    c.jy = (a.jyp.value() - a.jym.value()) * rn;
-    c.jz = (D == 3) ? (a.jzp.value() - a.jzm.value()) * rn : df(0.f, 0.f);
-    const df e2n = (a.e1.value() + scale2(a.e2.value(), 2.f)) * rn;
+    c.jx = Jx * rn;
+    c.jy = Jy * rn;
+    c.jz = (D == 3) ? Jz * rn : df(0.f, 0.f);
+    const df e2n = E * rn;
     const df jj = (D == 3) ? c.jx * c.jx + c.jy * c.jy + c.jz * c.jz : c.jx * c.jx + c.jy * c.jy;
     const df be = k.K * (e2n - jj);          // beta0 * eps
     const df a2 = (be - k.c) * k.inv_mc2;    // alpha2
@@ -219,6 +222,14 @@ template <int D> __device__ __forceinline__ DFCoef df_coefficients(const DFSums 
     if (!(n.hi > 0.f)) c.flag |= (n.hi == n.hi) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;
     if (!(fabsf(Sx.hi) + fabsf(Sy.hi) + fabsf(Sz.hi) + fabsf(be.hi) < 1e30f)) c.flag |= FLAG_NONFINITE;
     return c;
+}
+
+template <int D> __device__ __forceinline__ DFCoef df_coefficients(const DFSums &a, const Coll<df> &k)
+{
+    return df_coefficients_of<D>(a.n.value(), a.Sx.value(), a.Sy.value(), a.Sz.value(),
+                                 a.jxp.value() - a.jxm.value(), a.jyp.value() - a.jym.value(),
+                                 (D == 3) ? a.jzp.value() - a.jzm.value() : df(0.f, 0.f),
+                                 a.e1.value() + scale2(a.e2.value(), 2.f), k);
 }
 
 // Updates direction q (q <= (Q-1)/2) and its opposite Q-1-q in place; for

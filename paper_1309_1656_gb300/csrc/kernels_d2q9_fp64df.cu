@@ -15,12 +15,18 @@ template <int D> cudaError_t step_f64df(qlbm_ctx *h, bool odd)
     const dim3 blk(kF64dfBlock), grd((unsigned)((int64_t)g.nxb * g.ny * g.nz));
     const Planes<double, Lattice<D>::Q> pl = Launchers<D, CodecF64>::planes(h);
     const Coll<df> k = make_coll<df>(h);
+    const Coll<double> kd = make_coll<double>(h);
+    F64dfConst kc;
+    for (int i = 0; i < 2; ++i) {
+        kc.wc3[i] = df(kd.w[i + 1] * kd.c3);
+        kc.wc4[i] = df(kd.w[i + 1] * kd.c4);
+    }
     if (h->mag) {
-        if (odd) k_step_aa_f64df<D, true, true><<<grd, blk, 0, h->stream>>>(pl, g, k, h->flags);
-        else k_step_aa_f64df<D, false, true><<<grd, blk, 0, h->stream>>>(pl, g, k, h->flags);
+        if (odd) k_step_aa_f64df<D, true, true><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
+        else k_step_aa_f64df<D, false, true><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
     } else {
-        if (odd) k_step_aa_f64df<D, true, false><<<grd, blk, 0, h->stream>>>(pl, g, k, h->flags);
-        else k_step_aa_f64df<D, false, false><<<grd, blk, 0, h->stream>>>(pl, g, k, h->flags);
+        if (odd) k_step_aa_f64df<D, true, false><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
+        else k_step_aa_f64df<D, false, false><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
     }
     return cudaGetLastError();
 }
