@@ -178,32 +178,6 @@ template <int D> struct F64dfSplit {
 constexpr int kF64dfBlock = 64;                 // two warps
 template <int D> constexpr int f64df_min_blocks() { return D == 3 ? 9 : 12; }
 
-// Offsets from a site to its periodic neighbours one step along each axis
-// (formed once per thread), and the two neighbours x + e, x - e of a
-// lattice vector e with components in {-1, 0, 1}, by selects: the loops
-// over directions take their vectors at run time.
-struct NbOff {
-    int xp, xm, yp, ym, zp, zm;
-};
-__device__ __forceinline__ NbOff nb_offsets(const Grid &g, const SiteIdx &si)
-{
-    NbOff o;
-    const int nxy = g.nx * g.ny;
-    o.xp = si.x == g.nx - 1 ? 1 - g.nx : 1;
-    o.xm = si.x == 0 ? g.nx - 1 : -1;
-    o.yp = si.y == g.ny - 1 ? (1 - g.ny) * g.nx : g.nx;
-    o.ym = si.y == 0 ? (g.ny - 1) * g.nx : -g.nx;
-    o.zp = si.z == g.nz - 1 ? (1 - g.nz) * nxy : nxy;
-    o.zm = si.z == 0 ? (g.nz - 1) * nxy : -nxy;
-    return o;
-}
-__device__ __forceinline__ int nb_axis(int e, int plus, int minus) { return e > 0 ? plus : (e < 0 ? minus : 0); }
-__device__ __forceinline__ void nb_pair(const NbOff &o, int s, int ex, int ey, int ez, int &sp, int &sm)
-{
-    sp = s + nb_axis(ex, o.xp, o.xm) + nb_axis(ey, o.yp, o.ym) + nb_axis(ez, o.zp, o.zm);
-    sm = s + nb_axis(ex, o.xm, o.xp) + nb_axis(ey, o.ym, o.yp) + nb_axis(ez, o.zm, o.zp);
-}
-
 // Partial moment sums of the FP64_DF step, formed per direction group:
 // r = f of the rest direction; a1, a2 = f_i + f_-i summed over the pairs
 // with |i|^2 = 1, 2; J = sum over pairs of i (f_i - f_-i); S = sum of s_i.

@@ -59,6 +59,44 @@ __device__ __forceinline__ int neighbour(const Grid &g, const SiteIdx &si, int d
     return x + g.nx * (y + g.ny * z);
 }
 
+// Offsets from a site to its periodic neighbours one step along each axis
+// (x +- 1, y +- 1, z +- 1, wrapped), so that a neighbour's index is the
+// site's plus one offset per nonzero component.  In loops over directions
+// unrolled at compile time the selects below vanish; where the direction
+// is known only at run time they are a few selects, no division and no
+// multiplication.
+struct NbOff {
+    int xp, xm, yp, ym, zp, zm;
+};
+__device__ __forceinline__ void nb_offsets_yz(const Grid &g, int y, int z, NbOff &o)
+{
+    const int nxy = g.nx * g.ny;
+    o.yp = y == g.ny - 1 ? (1 - g.ny) * g.nx : g.nx;
+    o.ym = y == 0 ? (g.ny - 1) * g.nx : -g.nx;
+    o.zp = z == g.nz - 1 ? (1 - g.nz) * nxy : nxy;
+    o.zm = z == 0 ? (g.nz - 1) * nxy : -nxy;
+}
+__device__ __forceinline__ NbOff nb_offsets(const Grid &g, const SiteIdx &si)
+{
+    NbOff o;
+    o.xp = si.x == g.nx - 1 ? 1 - g.nx : 1;
+    o.xm = si.x == 0 ? g.nx - 1 : -1;
+    nb_offsets_yz(g, si.y, si.z, o);
+    return o;
+}
+__device__ __forceinline__ int nb_axis(int e, int plus, int minus) { return e > 0 ? plus : (e < 0 ? minus : 0); }
+// Index of site s + e (components of e in {-1, 0, 1}).
+__device__ __forceinline__ int nb_at(const NbOff &o, int s, int ex, int ey, int ez)
+{
+    return s + nb_axis(ex, o.xp, o.xm) + nb_axis(ey, o.yp, o.ym) + nb_axis(ez, o.zp, o.zm);
+}
+// Indices of s + e and s - e.
+__device__ __forceinline__ void nb_pair(const NbOff &o, int s, int ex, int ey, int ez, int &sp, int &sm)
+{
+    sp = s + nb_axis(ex, o.xp, o.xm) + nb_axis(ey, o.yp, o.ym) + nb_axis(ez, o.zp, o.zm);
+    sm = s + nb_axis(ex, o.xm, o.xp) + nb_axis(ey, o.ym, o.yp) + nb_axis(ez, o.zm, o.zp);
+}
+
 // Gathers the b populations of site si at the current time, in arithmetic
 // type R.  SWAPPED selects the reading pattern of a buffer last written by
 // an even step.
@@ -152,18 +190,18 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Starts the copies of the b stored vectors of site si (the slots an even
-// step reads at x, or an odd step reads at x + e_q) into dst[q * stride].
+// Starts the copies of the b stored vectors of site s (the slots an even
+// step reads at x, or an odd step reads at x + e_q; o: the site's
+// neighbour offsets) into dst[q * stride].
 template <int D, class Codec, bool SWAPPED>
-__device__ __forceinline__ void fetch_site(const Planes<typename Codec::S, Lattice<D>::Q> &pl,
-                                           const Grid &g, const SiteIdx &si,
-                                           typename QuadOf<typename Codec::S>::V *dst, int stride)
+__device__ __forceinline__ void fetch_site(const Planes<typename Codec::S, Lattice<D>::Q> &pl, int s,
+                                           const NbOff &o, typename QuadOf<typename Codec::S>::V *dst, int stride)
 {
     using V = typename QuadOf<typename Codec::S>::V;
 #pragma unroll
     for (int q = 0; q < Lattice<D>::Q; ++q) {
-        const int s = SWAPPED ? neighbour(g, si, cx<D>(q), cy<D>(q), cz<D>(q)) : si.s;
-        cp_async_vec<sizeof(V)>(dst + q * stride, pl.p[q] + s);
+        const int i = SWAPPED ? nb_at(o, s, cx<D>(q), cy<D>(q), cz<D>(q)) : s;
+        cp_async_vec<sizeof(V)>(dst + q * stride, pl.p[q] + i);
     }
 }
 
@@ -200,30 +238,45 @@ k_step_aa_rows(const Planes<typename Codec::S, Lattice<D>::Q> pl, Grid g, Coll<t
     if (x >= g.nx) return;
     const int row0 = grp * rpb;
     const int rend = min(row0 + rpb, g.ny * g.nz);
-    fetch_site<D, Codec, ODD>(pl, g, site_at(g, x, row0), mine, bw);
+    // the current row's coordinates and neighbour offsets, advanced row by
+    // row (one division, at the start)
+    SiteIdx cur = site_at(g, x, row0);
+    NbOff o = nb_offsets(g, cur);
+    fetch_site<D, Codec, ODD>(pl, cur.s, o, mine, bw);
     cp_async_commit();
     unsigned flag = 0;
     for (int row = row0, t = 0; row < rend; ++row, t ^= 1) {
-        if (row + 1 < rend) fetch_site<D, Codec, ODD>(pl, g, site_at(g, x, row + 1), mine + (t ^ 1) * Q * bw, bw);
+        int ny1 = cur.y + 1, nz1 = cur.z;
+        if (ny1 == g.ny) {
+            ny1 = 0;
+            ++nz1;
+        }
+        NbOff on = o;
+        nb_offsets_yz(g, ny1, nz1, on);
+        if (row + 1 < rend) fetch_site<D, Codec, ODD>(pl, cur.s + g.nx, on, mine + (t ^ 1) * Q * bw, bw);
         cp_async_commit();
         cp_async_wait<1>();     // this row's copies have landed
         R f[Q], sx[Q], sy[Q], sz[Q];
-        const V *cur = mine + t * Q * bw;
+        const V *cv = mine + t * Q * bw;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int p = ODD ? opposite<D>(q) : q;     // population held by slot q
-            codec.decode4(cur[q * bw], f[p], sx[p], sy[p], sz[p]);
+            codec.decode4(cv[q * bw], f[p], sx[p], sy[p], sz[p]);
         }
         flag |= Codec::template collide<D>(f, sx, sy, sz, k);
-        apply_field<D, FIELD, R>(sx, sy, sz, k, row * g.nx + x);
+        apply_field<D, FIELD, R>(sx, sy, sz, k, cur.s);
         // store addresses recomputed from g.zero (see k_step_aa)
-        const SiteIdx so = site_at(g, x + g.zero, row);
+        const int so = cur.s + g.zero;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int slot = ODD ? q : opposite<D>(q);
-            const int s = ODD ? neighbour(g, so, cx<D>(q), cy<D>(q), cz<D>(q)) : so.s;
-            codec.store4(pl.p[slot] + s, f[q], sx[q], sy[q], sz[q]);
+            const int i = ODD ? nb_at(o, so, cx<D>(q), cy<D>(q), cz<D>(q)) : so;
+            codec.store4(pl.p[slot] + i, f[q], sx[q], sy[q], sz[q]);
         }
+        cur.y = ny1;
+        cur.z = nz1;
+        cur.s += g.nx;
+        o = on;
     }
     if (flag) atomicOr(flags, flag);
 }
