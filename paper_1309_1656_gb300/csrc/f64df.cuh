@@ -178,6 +178,37 @@ template <int D> struct F64dfSplit {
 constexpr int kF64dfBlock = 64;                 // two warps
 template <int D> constexpr int f64df_min_blocks() { return D == 3 ? 9 : 12; }
 
+// Neighbour indices s + e, s - e for directions known only at run time.  A
+// warp's sites share one row, so where the row is away from the y (and,
+// for D3Q19, z) faces the whole warp takes s +- (e_x + e_y nx + e_z nx ny)
+// plus its lane's x-wrap correction (nonzero only at the row's ends);
+// other rows take the per-axis offsets.
+struct NbRt {
+    NbOff o;
+    int cxp, cxm;    // x-wrap corrections of a +x / -x step
+    bool interior;   // no y or z wrapping (the same in every lane of the warp)
+};
+template <int D> __device__ __forceinline__ NbRt nb_rt(const Grid &g, const SiteIdx &si)
+{
+    NbRt n;
+    n.o = nb_offsets(g, si);
+    n.cxp = si.x == g.nx - 1 ? -g.nx : 0;
+    n.cxm = si.x == 0 ? g.nx : 0;
+    n.interior = si.y > 0 && si.y < g.ny - 1 && (D == 2 || (si.z > 0 && si.z < g.nz - 1));
+    return n;
+}
+__device__ __forceinline__ void nb_pair_rt(const NbRt &n, const Grid &g, int s, int ex, int ey, int ez, int &sp,
+                                           int &sm)
+{
+    if (n.interior) {
+        const int d = ex + (ey + ez * g.ny) * g.nx;
+        sp = s + d + (ex > 0 ? n.cxp : (ex < 0 ? n.cxm : 0));
+        sm = s - d + (ex > 0 ? n.cxm : (ex < 0 ? n.cxp : 0));
+    } else {
+        nb_pair(n.o, s, ex, ey, ez, sp, sm);
+    }
+}
+
 // Partial moment sums of the FP64_DF step, formed per direction group:
 // r = f of the rest direction; a1, a2 = f_i + f_-i summed over the pairs
 // with |i|^2 = 1, 2; J = sum over pairs of i (f_i - f_-i); S = sum of s_i.
@@ -203,13 +234,13 @@ struct DfGroup {
 // an odd one (the buffer after an even step holds population p in slot
 // opposite(p) at x - e_p).
 template <int D, bool ODD>
-__device__ __forceinline__ void group_sources(const DQuad *base, const Grid &g, const NbOff &o, int s, int q,
+__device__ __forceinline__ void group_sources(const DQuad *base, const Grid &g, const NbRt &o, int s, int q,
                                               const DQuad *&pq, const DQuad *&pb)
 {
     constexpr int Q = Lattice<D>::Q;
     const int qb = Q - 1 - q;
     int sp = s, sm = s;
-    if (ODD) nb_pair(o, s, kDirs<D>.v[q][0], kDirs<D>.v[q][1], kDirs<D>.v[q][2], sp, sm);
+    if (ODD) nb_pair_rt(o, g, s, kDirs<D>.v[q][0], kDirs<D>.v[q][1], kDirs<D>.v[q][2], sp, sm);
     pq = base + (int64_t)(ODD ? qb : q) * g.P + sm;
     pb = base + (int64_t)(ODD ? q : qb) * g.P + sp;
 }
@@ -263,7 +294,7 @@ __device__ __forceinline__ DfGroup split_group(int q, unsigned amask, double2 r0
 // each group's values in place (a pair takes the 8 bytes of its double) and
 // adds them to the partial sums.  A thread reads back only what it copied.
 template <int D, bool ODD>
-__device__ __forceinline__ void f64df_pass1(const DQuad *base, const Grid &g, int s, const NbOff &o, int glo,
+__device__ __forceinline__ void f64df_pass1(const DQuad *base, const Grid &g, int s, const NbRt &o, int glo,
                                             int ghi, unsigned amask, double2 (*stage)[2][32], F64dfSums &a)
 {
     constexpr int Q = Lattice<D>::Q;
@@ -369,7 +400,7 @@ __device__ __forceinline__ F64dfCoef f64df_coefficients(const F64dfSums &a, cons
 // at x + e_q (odd), its opposite likewise.
 template <int D, bool ODD, bool MAG>
 __device__ __forceinline__ void update_group(int q, DfGroup &G, const F64dfCoef &c, const F64dfConst &kc,
-                                             const Coll<df> &k, DQuad *base, const Grid &g, const NbOff &o, int s)
+                                             const Coll<df> &k, DQuad *base, const Grid &g, const NbRt &o, int s)
 {
     constexpr int Q = Lattice<D>::Q;
     const int qb = Q - 1 - q;
@@ -411,7 +442,7 @@ __device__ __forceinline__ void update_group(int q, DfGroup &G, const F64dfCoef 
         if (pair) rotate_one(v[5], v[6], v[7], k.rot);
     }
     int sp = s, sm = s;
-    if (ODD) nb_pair(o, s, ex, ey, ez, sp, sm);
+    if (ODD) nb_pair_rt(o, g, s, ex, ey, ez, sp, sm);
     stq(base + (int64_t)(ODD ? q : qb) * g.P + sp, df_round(v[0]), df_round(v[1]), df_round(v[2]), df_round(v[3]));
     if (pair)
         stq(base + (int64_t)(ODD ? qb : q) * g.P + sm, df_round(v[4]), df_round(v[5]), df_round(v[6]),
@@ -453,7 +484,7 @@ k_step_aa_f64df(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<df> k, F64d
     double2(*const mine)[2][32] = stage + (SP::W == 2 ? (warp == 0 ? 0 : 2 * SP::G0) : warp * Lattice<D>::Q);
     F64dfSums a;
     a.zero();
-    const NbOff o = nb_offsets(g, si);
+    const NbRt o = nb_rt<D>(g, si);
     if (active) f64df_pass1<D, ODD>(base, g, si.s, o, glo, ghi, amask, mine, a);
     unsigned flag = 0u;
     if constexpr (SP::W == 2) {
