@@ -128,9 +128,9 @@ def test_fp64df_magnetic_field_vs_oracle(q, oracle_mod, d, dims):
 
 
 def test_fp64df_values_outside_the_split_range(q, oracle_mod):
-    # zero spin components and populations below 2^-74 take the conversion
-    # instructions instead of the bit-field split; the step must still
-    # follow the oracle
+    # zero spin components take the short split; values below 2^-74 (and
+    # the whole warp that holds one) take the general split; the step must
+    # still follow the oracle
     d, dims = 2, (40, 9, 1)
     st = fields.random_populations(d, dims, seed=13)
     st[:, 3, ::3] = 0.0           # s_z exactly zero at every third site
@@ -141,6 +141,45 @@ def test_fp64df_values_outside_the_split_range(q, oracle_mod):
         got = lat.get_state()
     exp = oracle_mod.run(d, dims, 0.7, 1.0, 4, st)
     assert rel(got, exp) < 4e-12
+
+
+def test_fp64df_small_spin_field_keeps_its_own_precision(q, oracle_mod):
+    # a spin field ~2^-75 below the densities (the general split, whose
+    # pairs are exact to 2^-47 down to 2^-102) must still be followed to
+    # double-float precision relative to its own size, up to the absolute
+    # floor of single precision's range (a lo part below 2^-126 is dropped
+    # when rounding back: ~1e-38, here ~1e-14 of the spins).  The oracle's
+    # complex-matrix storage resolves s_z only to ~ulp(f) (it sits in
+    # rho_11 - rho_22), so the expectation uses the step's exact linearity in
+    # the spins (u and eps depend on the traces alone, Eq. DiscrAvr):
+    # s(T) for lam * s(0) is lam * s(T) for s(0), with f(T) unchanged
+    d, dims = 3, (9, 7, 5)
+    st = fields.random_populations(d, dims, seed=21)
+    lam = 1e-22
+    small = st.copy()
+    small[:, 1:] *= lam
+    with q.Lattice(d, dims, 0.7, 1.0, precision="fp64df") as lat:
+        lat.set_state(small)
+        lat.step(3)
+        got = lat.get_state()
+    exp = oracle_mod.run(d, dims, 0.7, 1.0, 3, st)
+    assert rel(got[:, 0], exp[:, 0]) < 3e-12
+    assert rel(got[:, 1:], lam * exp[:, 1:]) < 3e-12
+
+
+def test_fp64df_values_below_the_float_range_become_zero(q, oracle_mod):
+    # double-float has single precision's exponent range: magnitudes below
+    # 2^-126 are read as signed zeros (the densities are unaffected)
+    d, dims = 2, (33, 5, 1)
+    st = fields.random_populations(d, dims, seed=22)
+    st[:, 1:] *= 1e-40
+    with q.Lattice(d, dims, 0.7, 1.0, precision="fp64df") as lat:
+        lat.set_state(st)
+        lat.step(2)
+        got = lat.get_state()
+    exp = oracle_mod.run(d, dims, 0.7, 1.0, 2, st)
+    assert rel(got[:, 0], exp[:, 0]) < 3e-12
+    assert np.all(np.abs(got[:, 1:]) < 2.0 ** -126)
 
 
 def test_fp64df_fd_path_is_the_fp64_one(q):
