@@ -717,6 +717,16 @@ def cpu_baseline(w, target_s=15.0, parity_fn=None):
     out = {"value": round(N * n / dt / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
            "sample": "%s sub-lattice %s of the same workload recipe, %d FP64 steps, %.1f s" %
                      ("D3Q19" if d == 3 else "D2Q9", "x".join(map(str, dims)), n, dt)}
+    # the same sample on one thread, over a shorter bounded time
+    n1, chunk, dt1 = 0, 1, 0.0
+    while dt1 < target_s / 4:
+        t = time.perf_counter()
+        st = oracle.run(d, dims, w["tau"], w["beta0"], chunk, st, nthreads=1)
+        dt1 += time.perf_counter() - t
+        n1 += chunk
+        chunk = min(2 * chunk, 512)
+    out["single_thread"] = {"value": round(N * n1 / dt1 / 1e6, 3), "unit": "MLUPS", "cores": 1,
+                            "steps": n1, "seconds": round(dt1, 2)}
     if parity_fn is not None:   # 1000 steps: the fields have not yet relaxed away
         st = oracle.init_equilibrium(d, dims, w["beta0"], fl["rho4"], fl["u"], fl["eps"])
         st = oracle.run(d, dims, w["tau"], w["beta0"], 1000, st)
