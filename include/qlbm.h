@@ -77,7 +77,11 @@ typedef enum qlbm_lattice { QLBM_D2Q9 = 2, QLBM_D3Q19 = 3 } qlbm_lattice;
    moments, reductions and Fermi-Dirac kernels) but steps in double-float
    arithmetic: each double is split into two floats, the step runs on the
    single-precision pipes and rounds its result to double (within ~1e-14 of
-   the QLBM_FP64 step per step; no reverse mode). */
+   the QLBM_FP64 step per step; no reverse mode).  Both double-float
+   precisions have single precision's exponent range: magnitudes below
+   2^-126 (~1.2e-38) are read as signed zeros and every stepped value
+   carries an absolute error up to ~2^-126 besides the relative one;
+   magnitudes from 2^128 on are flagged as non-finite. */
 typedef enum qlbm_precision {
     QLBM_FP64 = 0,
     QLBM_FP32 = 1,
