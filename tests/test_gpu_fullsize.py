@@ -103,7 +103,7 @@ def storage_tol(oracle_mod, d, beta0, exp, prec):
     balance, collects the float (u_a = 2^-24) roundings of a b-term sum
     plus two more operations.  Over the two steps, normwise relative to the
     largest population:  2 ((b + 2) u_a + u_s) D / max|W|."""
-    if prec in ("fp64", "fp64df"):
+    if prec in ("fp64", "fp64df", "df64"):
         return 2e-12
     c = oracle_mod.constants(d, beta0)
     w, b = c["w"], c["b"]
@@ -114,7 +114,7 @@ def storage_tol(oracle_mod, d, beta0, exp, prec):
     return 2.0 * ((b + 2) * ua + us) * np.max(np.abs(dev)) / np.max(np.abs(exp))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp64df", "fp32", "fp16dev"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64df", "df64", "fp32", "fp16dev"])
 def test_d3q19_128_bench_configuration(q, oracle_mod, prec):
     d, dims, tau, beta0 = 3, (128, 128, 128), 0.7, 1.0
     fl = fields.modes(3, dims, seed=2)
@@ -125,7 +125,7 @@ def test_d3q19_128_bench_configuration(q, oracle_mod, prec):
     check(got, exp, storage_tol(oracle_mod, d, beta0, exp, prec))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16dev"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16dev", "df64", "fp64df"])
 def test_d2q9_4096_shear_layer(q, oracle_mod, prec):
     d, dims, tau, beta0 = 2, (4096, 4096, 1), 0.7, 1.0
     fl = fields.shear2d(4096, 4096, seed=3)
