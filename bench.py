@@ -34,8 +34,9 @@ Every leg after the first times at least --leg-ms of steps so that the
 nvidia-smi clock samples fall inside its timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun (N > 1) every rank runs an independent replica (the path has
-no exchange step in this build); value = all ranks' site updates / max time.
+Under torchrun (N > 1) every rank runs an independent replica (no halo
+exchange between ranks is implemented); value = all ranks' site updates /
+max time.
 """
 import argparse
 import hashlib

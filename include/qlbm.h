@@ -55,7 +55,7 @@ extern "C" {
 typedef enum qlbm_status {
     QLBM_OK = 0,
     QLBM_ERR_INVALID_ARG = -1,        /* bad size, pointer, parameter or lattice */
-    QLBM_ERR_UNSUPPORTED = -2,        /* combination not provided by this build */
+    QLBM_ERR_UNSUPPORTED = -2,        /* combination not provided by the library */
     QLBM_ERR_OOM = -3,                /* device allocation failed */
     QLBM_ERR_CUDA = -4,               /* a CUDA runtime call failed */
     QLBM_ERR_NONFINITE = -5,          /* a step met a NaN or infinite moment */

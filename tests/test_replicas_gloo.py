@@ -1,5 +1,5 @@
-"""The N > 1 path of bench.py on CPU: independent replicas (the step has no
-exchange in this build), the job's time is the slowest rank's, and the
+"""The N > 1 path of bench.py on CPU: independent replicas (no halo exchange
+between ranks is implemented), the job's time is the slowest rank's, and the
 job's value counts every rank's site updates.  Two gloo ranks over
 127.0.0.1; the reference arm runs on rank 0 only."""
 import os
