@@ -119,6 +119,28 @@ __device__ __forceinline__ df lin2(df a, df x, df b, df y)
     return df(s.hi, __fadd_rn(s.lo, __fadd_rn(e1, e2)));
 }
 
+// a0 x0 + a1 x1 + a2 x2 with each product exact to ~2^-48 (Dekker) and two
+// TwoSums of the leading parts, left unnormalised like lin2.
+__device__ __forceinline__ df dot3(df a0, df x0, df a1, df x1, df a2, df x2)
+{
+    const float p0 = __fmul_rn(a0.hi, x0.hi), p1 = __fmul_rn(a1.hi, x1.hi), p2 = __fmul_rn(a2.hi, x2.hi);
+    float e0 = __fmaf_rn(a0.hi, x0.hi, -p0), e1 = __fmaf_rn(a1.hi, x1.hi, -p1), e2 = __fmaf_rn(a2.hi, x2.hi, -p2);
+    e0 = __fmaf_rn(a0.hi, x0.lo, __fmaf_rn(a0.lo, x0.hi, e0));
+    e1 = __fmaf_rn(a1.hi, x1.lo, __fmaf_rn(a1.lo, x1.hi, e1));
+    e2 = __fmaf_rn(a2.hi, x2.lo, __fmaf_rn(a2.lo, x2.hi, e2));
+    const df s = two_sum(p0, p1), t = two_sum(s.hi, p2);
+    return df(t.hi, __fadd_rn(__fadd_rn(s.lo, t.lo), __fadd_rn(e0, __fadd_rn(e1, e2))));
+}
+
+// The spin (x, y, z) rotated by the 3x3 matrix r (row-major), with dot3.
+__device__ __forceinline__ void rotate_raw(df &x, df &y, df &z, const df (&r)[9])
+{
+    const df a = x, b = y, c = z;
+    x = dot3(r[0], a, r[1], b, r[2], c);
+    y = dot3(r[3], a, r[4], b, r[5], c);
+    z = dot3(r[6], a, r[7], b, r[8], c);
+}
+
 // x + y without the final renormalisation (8 operations).
 __device__ __forceinline__ df add_raw(df x, df y)
 {
@@ -398,9 +420,10 @@ __device__ __forceinline__ F64dfCoef f64df_coefficients(const F64dfSums &a, cons
 // value, the step's only FP64 arithmetic) and stored where the AA pattern
 // puts them: population q to slot opposite(q) at x (even step) or slot q
 // at x + e_q (odd), its opposite likewise.
-template <int D, bool ODD, bool MAG>
+template <int D, bool ODD, int FIELD>
 __device__ __forceinline__ void update_group(int q, DfGroup &G, const F64dfCoef &c, const F64dfConst &kc,
-                                             const Coll<df> &k, DQuad *base, const Grid &g, const NbRt &o, int s)
+                                             const Coll<df> &k, const df (&rs)[9], DQuad *base, const Grid &g,
+                                             const NbRt &o, int s)
 {
     constexpr int Q = Lattice<D>::Q;
     const int qb = Q - 1 - q;
@@ -435,11 +458,18 @@ __device__ __forceinline__ void update_group(int q, DfGroup &G, const F64dfCoef 
         v[6] = lin2(c.omc, v[6], hm, c.oSy);
         v[7] = lin2(c.omc, v[7], hm, c.oSz);
     }
-    if constexpr (MAG) {
+    if constexpr (FIELD != FIELD_NONE) {
+        // the field term: the spins rotated by the uniform matrix or by the
+        // site's own (rs)
 #pragma unroll
         for (int i = 1; i < 8; ++i) v[i] = two_sum(v[i].hi, v[i].lo);
-        rotate_one(v[1], v[2], v[3], k.rot);
-        if (pair) rotate_one(v[5], v[6], v[7], k.rot);
+        if constexpr (FIELD == FIELD_SITE) {
+            rotate_raw(v[1], v[2], v[3], rs);
+            if (pair) rotate_raw(v[5], v[6], v[7], rs);
+        } else {
+            rotate_raw(v[1], v[2], v[3], k.rot);
+            if (pair) rotate_raw(v[5], v[6], v[7], k.rot);
+        }
     }
     int sp = s, sm = s;
     if (ODD) nb_pair_rt(o, g, s, ex, ey, ez, sp, sm);
@@ -459,7 +489,7 @@ __device__ __forceinline__ void update_group(int q, DfGroup &G, const F64dfCoef 
 // update_group.  Each value is read from and written to HBM once.  In the
 // AA pattern a pair's read locations are its write locations, so the
 // pairwise in-place update is race-free (as in k_step_aa_df2).
-template <int D, bool ODD, bool MAG>
+template <int D, bool ODD, int FIELD>
 __global__ void __launch_bounds__(kF64dfBlock, f64df_min_blocks<D>())
 k_step_aa_f64df(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<df> k, F64dfConst kc,
                 unsigned *__restrict__ flags)
@@ -498,6 +528,15 @@ k_step_aa_f64df(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<df> k, F64d
         if (!active) return;
     }
     const F64dfCoef c = f64df_coefficients<D>(a, k, flag);
+    // a per-site field: the site's rotation from its unit quaternion (stored
+    // as doubles), split with the integer split and formed in double-float
+    // (no work on the double pipe, which the rounding back already uses)
+    df rs[9];
+    if constexpr (FIELD == FIELD_SITE) {
+        double w, x, y, z;
+        load_quat(k.qf + si.s, w, x, y, z);
+        quat_rotation(df_of_double(w), df_of_double(x), df_of_double(y), df_of_double(z), rs);
+    }
     // g.zero (0 at run time) keeps pass 2's addresses from being carried
     // over from pass 1 in registers
     const int s2 = si.s + g.zero;
@@ -518,7 +557,7 @@ k_step_aa_f64df(const Planes<double, Lattice<D>::Q> pl, Grid g, Coll<df> k, F64d
             G.v[6] = df(b1.x, b1.y);
             G.v[7] = df(b1.z, b1.w);
         }
-        update_group<D, ODD, MAG>(q, G, c, kc, k, base, g, o, s2);
+        update_group<D, ODD, FIELD>(q, G, c, kc, k, rs, base, g, o, s2);
     }
     if (flag && (SP::W == 1 || warp == 0)) atomicOr(flags, flag);
 }

@@ -21,14 +21,12 @@ template <int D> cudaError_t step_f64df(qlbm_ctx *h, bool odd)
         kc.wc3[i] = df(kd.w[i + 1] * kd.c3);
         kc.wc4[i] = df(kd.w[i + 1] * kd.c4);
     }
-    if (h->mag) {
-        if (odd) k_step_aa_f64df<D, true, true><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
-        else k_step_aa_f64df<D, false, true><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
-    } else {
-        if (odd) k_step_aa_f64df<D, true, false><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
-        else k_step_aa_f64df<D, false, false><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
-    }
-    return cudaGetLastError();
+    return with_field(h->mag, [&](auto fc) {
+        constexpr int F = decltype(fc)::value;
+        if (odd) k_step_aa_f64df<D, true, F><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
+        else k_step_aa_f64df<D, false, F><<<grd, blk, 0, h->stream>>>(pl, g, k, kc, h->flags);
+        return cudaGetLastError();
+    });
 }
 template cudaError_t step_f64df<3>(qlbm_ctx *h, bool odd);
 

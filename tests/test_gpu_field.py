@@ -102,13 +102,16 @@ def osite(oracle_mod):
     oracle_mod.set_field(0.0, (0, 0, 0))
 
 
-@pytest.mark.parametrize("d,dims", [(2, (37, 5, 1)), (3, (9, 7, 5))])
+@pytest.mark.parametrize("prec", ["fp64", "fp64df"])
+@pytest.mark.parametrize("d,dims", [(2, (37, 5, 1)), (3, (9, 7, 5)), (3, (33, 6, 4))])
 @pytest.mark.parametrize("nsteps", [1, 2, 7, 70])
-def test_site_field_fp64_vs_oracle(q, osite, d, dims, nsteps):
+def test_site_field_fp64_vs_oracle(q, osite, prec, d, dims, nsteps):
+    # FP64 storage stepped in double or in double-float arithmetic (within
+    # 1e-12 per step of the oracle either way)
     st = fields.random_populations(d, dims, seed=150 + d)
     Bs = site_field(dims, 3 + d)
     osite.set_field_array(MU, Bs)
-    with q.Lattice(d, dims, 0.75, 1.0, precision="fp64") as lat:
+    with q.Lattice(d, dims, 0.75, 1.0, precision=prec) as lat:
         lat.set_magnetic_field_array(MU, Bs)
         lat.set_state(st)
         lat.step(nsteps)
@@ -170,13 +173,14 @@ def test_site_field_fp16_vs_oracle(q, osite, d, dims):
     assert rel(got, exp) < tol
 
 
-def test_site_field_changing_in_time(q, osite):
+@pytest.mark.parametrize("prec", ["fp64", "fp64df"])
+def test_site_field_changing_in_time(q, osite, prec):
     # B(x, t): a new field before every step, on the GPU and in the oracle
     d, dims, n = 3, (8, 7, 5), 6
     st = fields.random_populations(d, dims, seed=16)
     B0 = site_field(dims, 11)
     exp = st
-    with q.Lattice(d, dims, 0.8, 1.0, precision="fp64") as lat:
+    with q.Lattice(d, dims, 0.8, 1.0, precision=prec) as lat:
         lat.set_state(st)
         for t in range(n):
             Bt = B0 * np.cos(0.7 * t) + 0.3 * np.sin(0.4 * t)
@@ -261,11 +265,10 @@ def test_site_field_arguments(q):
     d, dims = 2, (8, 6, 1)
     N = int(np.prod(dims))
     st = fields.random_populations(d, dims, seed=17)
-    for prec in ("df64", "fp64df"):
-        with q.Lattice(d, dims, 0.8, 1.0, precision=prec) as lat:
-            with pytest.raises(q.QLBMError) as e:
-                lat.set_magnetic_field_array(MU, np.ones((3, N)))
-            assert e.value.code == q.QLBM_ERR_UNSUPPORTED
+    with q.Lattice(d, dims, 0.8, 1.0, precision="df64") as lat:
+        with pytest.raises(q.QLBMError) as e:
+            lat.set_magnetic_field_array(MU, np.ones((3, N)))
+        assert e.value.code == q.QLBM_ERR_UNSUPPORTED
     with q.Lattice(d, dims, 0.8, 1.0, precision="fp64") as lat:
         bad = np.ones((3, N))
         bad[1, 5] = np.nan
