@@ -414,6 +414,7 @@ def bench_ours(args):
 
         r = bn.leg(d, dims, w["tau"], w["beta0"], "fp32", init_field, min_ms=args.leg_ms, extra_bytes=16)
         r["field"] = "B(x) per site, mu = 0.3, smooth (|B| ~ 0.1); 608 + 16 algorithmic bytes per site"
+        r["roofline"]["kernel"] = "k_step_aa<%d, CodecF32> (per-site field variant)" % d
         r["vs_no_field"] = round(r["_step_ms"] / results["fp32"]["_step_ms"], 3)
         extra["fp32_site_field"] = r
         del Bs
