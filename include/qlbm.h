@@ -229,14 +229,13 @@ int qlbm_set_magnetic_field(qlbm_handle h, double mu, const double B[3]);
  *       QLBM_ERR_INVALID_ARG and leave the field off
  * The library keeps, per site, the unit quaternion (cos phi, sin phi
  * B/|B|), phi = mu |B(x)| dt (16 bytes in single-precision storage, 32 in
- * FP64 storage), which each step reads once per site.  A field B(x, t) that changes
+ * the 64-bit precisions), which each step reads once per site.  A field B(x, t) that changes
  * in time is given by calling this again between steps: the new field
  * applies from the next step.  Applies to qlbm_step (both equilibrium
  * paths), qlbm_step_fd_output, qlbm_rollout and the reverse mode (which
  * uses the field set when the rollout was recorded: a call discards a
- * recorded rollout).  QLBM_FP64, QLBM_FP64_DF, QLBM_FP32 and QLBM_FP16_DEV
- * storage (QLBM_ERR_UNSUPPORTED for QLBM_DF64).  qlbm_set_magnetic_field
- * replaces it.
+ * recorded rollout).  Every storage precision (32 bytes per site for the
+ * 64-bit ones).  qlbm_set_magnetic_field replaces it.
  * Synchronising. */
 int qlbm_set_magnetic_field_array(qlbm_handle h, double mu, const double *B, int ptr_kind);
 

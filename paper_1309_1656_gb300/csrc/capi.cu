@@ -762,12 +762,10 @@ int qlbm_set_magnetic_field_array(qlbm_handle h, double mu, const double *B, int
     if (ptr_kind != QLBM_HOST && ptr_kind != QLBM_DEVICE) return fail(h, QLBM_ERR_INVALID_ARG, "bad ptr_kind");
     if (!(mu == mu) || !(fabs(mu) < 1e300))
         return fail(h, QLBM_ERR_INVALID_ARG, "qlbm_set_magnetic_field_array: mu must be finite");
-    if (h->prec == QLBM_DF64)
-        return fail(h, QLBM_ERR_UNSUPPORTED,
-                    "qlbm_set_magnetic_field_array: a per-site field needs QLBM_FP64, QLBM_FP64_DF, QLBM_FP32 or "
-                    "QLBM_FP16_DEV storage");
     const int64_t N = h->g.N;
-    const bool dbl = h->prec == QLBM_FP64 || h->prec == QLBM_FP64_DF;
+    // quaternions as doubles for the 64-bit precisions (the double-float
+    // steps split them), as floats for the single-precision arithmetic
+    const bool dbl = h->prec == QLBM_FP64 || h->prec == QLBM_FP64_DF || h->prec == QLBM_DF64;
     const size_t vb = dbl ? sizeof(DQuad) : sizeof(float4);
     if (!h->qfield) CK(h, cudaMalloc(&h->qfield, (size_t)N * vb));
     const double *src = B;

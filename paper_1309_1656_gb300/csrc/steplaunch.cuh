@@ -18,17 +18,14 @@ cudaError_t Launchers<D, Codec>::step(qlbm_ctx *h, bool odd)
     const Coll<R> k = make_coll<R>(h);
     const Codec codec = make_codec<Codec>(h);
     if constexpr (TwoPass<Codec>::value) {
-        if (h->mag) {
+        return with_field(h->mag, [&](auto fc) {
+            constexpr int F = decltype(fc)::value;
             if (odd)
-                k_step_aa_df2<D, true, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+                k_step_aa_df2<D, true, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
             else
-                k_step_aa_df2<D, false, true><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-        } else {
-            if (odd)
-                k_step_aa_df2<D, true, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-            else
-                k_step_aa_df2<D, false, false><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
-        }
+                k_step_aa_df2<D, false, F><<<grd, blk, 0, h->stream>>>(pl, h->g, k, codec, h->flags);
+            return cudaGetLastError();
+        });
     } else if constexpr (RowPipelined<Codec>::value) {
         // rows per block from a sweep on GB300 (FP16): D2Q9 4096^2 gains
         // 14 % at 8, D3Q19 192^3 - 256^3 4-7 % at 4 (more rows lose to the tail)

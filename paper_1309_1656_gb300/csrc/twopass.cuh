@@ -50,7 +50,7 @@ __device__ __forceinline__ int read_site(const Grid &g, const SiteIdx &si, int p
     return SWAPPED ? neighbour(g, si, -cx<D>(p), -cy<D>(p), -cz<D>(p)) : si.s;
 }
 
-template <int D, bool ODD, bool MAG>
+template <int D, bool ODD, int FIELD>
 __global__ void __launch_bounds__(kStepBlock, TwoPass<CodecDF>::min_blocks<D>())
 k_step_aa_df2(const Planes<df, Lattice<D>::Q> pl, Grid g, Coll<df> k, CodecDF codec, unsigned *__restrict__ flags)
 {
@@ -75,6 +75,16 @@ k_step_aa_df2(const Planes<df, Lattice<D>::Q> pl, Grid g, Coll<df> k, CodecDF co
         df_accumulate<D>(a, p, df(h.x, l.x), df(h.y, l.y), df(h.z, l.z), df(h.w, l.w));
     }
     const DFCoef c = df_coefficients<D>(a, k);
+    // a per-site field: the site's rotation, formed in double from its unit
+    // quaternion and rounded to double-float pairs
+    df rs[9];
+    if constexpr (FIELD == FIELD_SITE) {
+        double w, x, y, z, r[9];
+        load_quat(k.qf + si.s, w, x, y, z);
+        quat_rotation(w, x, y, z, r);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) rs[i] = df(r[i]);
+    }
     // g.zero (0 at run time) makes pass 2's addresses distinct expressions,
     // so the compiler re-loads the lo parts instead of keeping pass 1's.
     SiteIdx s2 = si;
@@ -96,9 +106,12 @@ k_step_aa_df2(const Planes<df, Lattice<D>::Q> pl, Grid g, Coll<df> k, CodecDF co
             zb = df(hz[qb], lb.w);
         }
         df_pair<D>(c, k, q, f, x, y, z, fb, xb, yb, zb);
-        if constexpr (MAG) {
+        if constexpr (FIELD == FIELD_UNIFORM) {
             rotate_one(x, y, z, k.rot);
             if (qb != q) rotate_one(xb, yb, zb, k.rot);
+        } else if constexpr (FIELD == FIELD_SITE) {
+            rotate_one(x, y, z, rs);
+            if (qb != q) rotate_one(xb, yb, zb, rs);
         }
         // population p goes to slot opposite(p) at x (even) or slot p at x + e_p (odd)
         codec.store4(pl.p[ODD ? q : qb] + (ODD ? neighbour(g, s2, cx<D>(q), cy<D>(q), cz<D>(q)) : s2.s), f, x, y,

@@ -102,12 +102,13 @@ def osite(oracle_mod):
     oracle_mod.set_field(0.0, (0, 0, 0))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp64df"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64df", "df64"])
 @pytest.mark.parametrize("d,dims", [(2, (37, 5, 1)), (3, (9, 7, 5)), (3, (33, 6, 4))])
 @pytest.mark.parametrize("nsteps", [1, 2, 7, 70])
 def test_site_field_fp64_vs_oracle(q, osite, prec, d, dims, nsteps):
-    # FP64 storage stepped in double or in double-float arithmetic (within
-    # 1e-12 per step of the oracle either way)
+    # the 64-bit precisions: FP64 storage stepped in double or in
+    # double-float arithmetic, and double-float storage (within 1e-12 per
+    # step of the oracle each)
     st = fields.random_populations(d, dims, seed=150 + d)
     Bs = site_field(dims, 3 + d)
     osite.set_field_array(MU, Bs)
@@ -173,7 +174,7 @@ def test_site_field_fp16_vs_oracle(q, osite, d, dims):
     assert rel(got, exp) < tol
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp64df"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64df", "df64"])
 def test_site_field_changing_in_time(q, osite, prec):
     # B(x, t): a new field before every step, on the GPU and in the oracle
     d, dims, n = 3, (8, 7, 5), 6
@@ -265,10 +266,6 @@ def test_site_field_arguments(q):
     d, dims = 2, (8, 6, 1)
     N = int(np.prod(dims))
     st = fields.random_populations(d, dims, seed=17)
-    with q.Lattice(d, dims, 0.8, 1.0, precision="df64") as lat:
-        with pytest.raises(q.QLBMError) as e:
-            lat.set_magnetic_field_array(MU, np.ones((3, N)))
-        assert e.value.code == q.QLBM_ERR_UNSUPPORTED
     with q.Lattice(d, dims, 0.8, 1.0, precision="fp64") as lat:
         bad = np.ones((3, N))
         bad[1, 5] = np.nan
