@@ -240,8 +240,8 @@ k_field_quaternions(const double *__restrict__ B, int64_t N, double mu_dt, V *__
 
 cudaError_t launch_conserved_final(qlbm_ctx *h)
 {
-    k_conserved_final<<<1, kRedBlock, 0, h->stream>>>(h->partials, h->nred, h->hc.xi, h->g.N,
-                                                      h->red_out);
+    k_conserved_final<<<1, kRedBlock, 0, h->stream>>>(h->partials, h->red_grid ? h->red_grid : h->nred, h->hc.xi,
+                                                      h->g.N, h->red_out);
     return cudaGetLastError();
 }
 

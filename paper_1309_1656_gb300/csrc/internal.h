@@ -45,7 +45,8 @@ struct qlbm_ctx {
     unsigned *flags = nullptr;      // device flag word
     double *partials = nullptr;     // device reduction scratch [nred][8]
     double *red_out = nullptr;      // device [8]
-    int nred = 0;
+    int nred = 0;                   // rows of partials (the most blocks a reduction launches)
+    int red_grid = 0;               // blocks of the reduction: whole waves of resident blocks, <= nred
     double *staging = nullptr;      // device staging for host inputs/outputs
     size_t staging_bytes = 0;
     const qlbm::LatticeOps *ops = nullptr;

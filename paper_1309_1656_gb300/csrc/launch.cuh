@@ -159,12 +159,24 @@ template <int D, class Codec> struct Launchers {
 
     static cudaError_t conserved_partial(qlbm_ctx *h)
     {
+        if (!h->red_grid) {
+            // one whole wave of resident blocks (a fixed count left a
+            // partial second wave); found once per handle
+            int a = 0, b = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_conserved_partial<D, Codec, false>,
+                                                                          kRedBlock, 0);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_conserved_partial<D, Codec, true>, kRedBlock, 0);
+            if (e != cudaSuccess) return e;
+            const int64_t wave = (int64_t)(a < b ? a : b) * h->sms;
+            h->red_grid = (int)(wave >= 1 && wave < h->nred ? wave : h->nred);
+        }
         const Planes<S, Q> pl = planes(h);
         if (h->parity)
-            k_conserved_partial<D, Codec, true><<<h->nred, kRedBlock, 0, h->stream>>>(
+            k_conserved_partial<D, Codec, true><<<h->red_grid, kRedBlock, 0, h->stream>>>(
                 pl, h->g, make_codec<Codec>(h), h->partials);
         else
-            k_conserved_partial<D, Codec, false><<<h->nred, kRedBlock, 0, h->stream>>>(
+            k_conserved_partial<D, Codec, false><<<h->red_grid, kRedBlock, 0, h->stream>>>(
                 pl, h->g, make_codec<Codec>(h), h->partials);
         return cudaGetLastError();
     }
